@@ -1,0 +1,196 @@
+/*
+ * spkadd.h -- C ABI of the GB300 SpKAdd library (libspkadd.so).
+ *
+ * SpKAdd (Sec. II-A of "Parallel Algorithms for Adding a Collection of Sparse
+ * Matrices"): B = A_1 + A_2 + ... + A_k for k sparse matrices of one shape
+ * m x n, all in CSC form; B is CSC with rows sorted ascending in every column.
+ * An output entry exists wherever at least one input has an entry (the union
+ * of the input patterns, Sec. II-A / Alg. 5); entries whose terms cancel are
+ * kept with value 0.  nnz(B) <= sum_i nnz(A_i) (Sec. II-A).
+ *
+ * The computation runs in phases, as the paper's k-way algorithms do:
+ *   spkadd_plan      -- per-column input counts and load-balancing classes
+ *                       (Sec. III-A: "in the symbolic phase we use total input
+ *                       non-zeros per column ... to balance loads").
+ *   spkadd_symbolic  -- nnz(B(:,j)) for every column (Alg. 6 HashSymbolic,
+ *                       Alg. 7 SlHashSymbolic for heavy columns, Sec. II-D),
+ *                       the exclusive scan into B's column pointers, and the
+ *                       total nnz(B), returned to the host so the caller can
+ *                       allocate B (Sec. II-D: "pre-allocate necessary memory").
+ *   spkadd_numeric   -- the values (Alg. 5 HashAdd, Alg. 8 SlHashAdd for heavy
+ *                       columns) and the per-column sort (Alg. 5, last step).
+ *   spkadd_destroy   -- releases the handle and its device workspace.
+ *
+ * Conventions for every entry point:
+ *   - Pointers documented "device" must point to memory of the current CUDA
+ *     device; "host" pointers to ordinary host memory.
+ *   - All device work of a handle is ordered on the stream given to
+ *     spkadd_plan (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream).  spkadd_symbolic synchronises that stream once to read nnz(B);
+ *     no other call blocks the host.
+ *   - Every call returns a status; nothing aborts, throws or traps.  A failed
+ *     kernel launch returns SPKADD_ERR_CUDA; errors raised asynchronously by
+ *     the device surface at the next call on the handle.
+ *   - Calls out of order (numeric before symbolic) return SPKADD_ERR_STATE.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef SPKADD_H
+#define SPKADD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spkadd_status {
+    SPKADD_OK = 0,
+    SPKADD_ERR_INVALID_ARG = 1,     /* null pointer, k < 1, negative size, bad option */
+    SPKADD_ERR_SHAPE_MISMATCH = 2,  /* inputs disagree on m or n */
+    SPKADD_ERR_UNSORTED = 3,        /* validate mode: a column's rows are not strictly increasing */
+    SPKADD_ERR_INDEX_RANGE = 4,     /* validate mode: row outside [0, m) or col_ptr not monotone / not ending at nnz */
+    SPKADD_ERR_OVERFLOW = 5,        /* m or n >= 2^31, or a column's input count >= 2^31 */
+    SPKADD_ERR_NOMEM = 6,           /* the workspace allocation failed */
+    SPKADD_ERR_CUDA = 7,            /* a CUDA runtime call or kernel launch failed */
+    SPKADD_ERR_TIMEOUT = 8,         /* a bounded device wait gave up */
+    SPKADD_ERR_STATE = 9,           /* call out of order */
+    SPKADD_ERR_UNSUPPORTED = 10,    /* valid request this build does not handle (e.g. k > SPKADD_MAX_K) */
+    SPKADD_ERR_INTERNAL = 11        /* a device-side size invariant failed; the result is not valid */
+} spkadd_status;
+
+typedef enum spkadd_dtype {
+    SPKADD_F32 = 0,   /* float values  (8 bytes per (row, value) pair, Sec. III-B's b = 8) */
+    SPKADD_F64 = 1    /* double values (12 bytes per pair, the Sec. IV-B example)        */
+} spkadd_dtype;
+
+/* Largest k one handle accepts. */
+#define SPKADD_MAX_K 65536
+
+/*
+ * One input matrix A_i in CSC form (Sec. II-A: a column is a list of
+ * (rowid, val) tuples).  All three arrays are device memory, borrowed: they
+ * must stay valid and unmodified until spkadd_numeric's work on the stream is
+ * done (or the handle is destroyed).
+ *   col_ptr[n+1]  int32, col_ptr[0] = 0, non-decreasing, col_ptr[n] = nnz
+ *   row_idx[nnz]  int32, in [0, m), strictly increasing inside each column
+ *   val[nnz]      float or double, as the plan's dtype says
+ * nnz may be 0 (row_idx and val may then be NULL).
+ */
+typedef struct spkadd_csc {
+    int64_t m;
+    int64_t n;
+    int64_t nnz;
+    const int32_t* col_ptr;
+    const int32_t* row_idx;
+    const void* val;
+} spkadd_csc;
+
+/*
+ * Tuning and behaviour knobs.  Fill with spkadd_default_options() and
+ * override fields; pass NULL to spkadd_plan for the defaults.
+ */
+typedef struct spkadd_options {
+    /* Nonzero: spkadd_plan checks every input on the device (one extra read
+     * of all row indices, then one stream synchronisation) and returns
+     * SPKADD_ERR_UNSORTED / SPKADD_ERR_INDEX_RANGE on bad input.  Zero: the
+     * inputs are trusted.  Then rows outside [0, m) or out of order give an
+     * unspecified B (shared-memory accesses stay in bounds), but col_ptr
+     * values outside [0, nnz] make the kernels read outside row_idx/val. */
+    int32_t validate;
+    /* Columns whose summed input count s_j = sum_i nnz(A_i(:,j)) is at most
+     * warp_max run one warp per column (range 1..512). */
+    int32_t warp_max;
+    /* Columns with warp_max < s_j <= cta_max run one thread block per column
+     * (range warp_max..4096).  Larger columns are "heavy": the symbolic pass
+     * uses a shared-memory row bitmap and the numeric pass splits them into
+     * row windows (Sec. III-B, sliding hash). */
+    int32_t cta_max;
+    /* Maximum distinct rows per numeric row window of a heavy column
+     * (range 1024..4096). */
+    int32_t window_max;
+    /* 0 = adaptive (order-preserving hash for columns whose rows spread
+     * evenly, scrambled hash + counting sort otherwise); 1 = always the
+     * scrambled hash + counting sort. */
+    int32_t sort_mode;
+    /* Workspace allocator.  NULL alloc: cudaMallocAsync / cudaFreeAsync on
+     * the plan's stream.  Otherwise alloc(bytes, stream, ctx) must return
+     * device memory usable on `stream` (or NULL on failure) and
+     * free(ptr, stream, ctx) releases it. */
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, void* stream, void* ctx);
+    void* alloc_ctx;
+} spkadd_options;
+
+/* Planning statistics (host copy), for tests and benchmarks. */
+typedef struct spkadd_info {
+    int64_t k, m, n;
+    int64_t nnz_in;         /* sum_i nnz(A_i) */
+    int64_t nnz_out;        /* nnz(B); -1 before spkadd_symbolic */
+    int64_t cols_warp;      /* columns per class (valid after spkadd_symbolic) */
+    int64_t cols_cta;
+    int64_t cols_heavy;
+    int64_t windows;        /* numeric thread-block work items (CTA columns + heavy windows) */
+    int64_t windows_split;  /* of those, row windows that needed per-input binary searches */
+    int64_t cols_ordered;   /* warp columns summed with the order-preserving hash */
+    int64_t workspace_bytes;
+    int64_t kernel_launches; /* kernels this handle has launched so far */
+} spkadd_info;
+
+typedef struct spkadd_handle spkadd_handle;
+
+/* Fills *opt with the defaults (validate 0, warp_max 512, cta_max 4096,
+ * window_max 4096, sort_mode 0, cudaMallocAsync).  No CUDA call. */
+void spkadd_default_options(spkadd_options* opt);
+
+/*
+ * Plans B = A[0] + ... + A[k-1].
+ *   h       host out: the new handle (set to NULL on failure)
+ *   k       number of inputs, 1 <= k <= SPKADD_MAX_K
+ *   A       host array of k descriptors (copied; the arrays they point to
+ *           are borrowed device memory, see spkadd_csc)
+ *   dtype   value type of every input and of B
+ *   stream  cudaStream_t (as void*) all work is ordered on
+ *   opt     NULL for defaults
+ * Host-side checks first (null pointers, k, shapes, sizes: no CUDA call is
+ * made when they fail); then the workspace is allocated and the column
+ * binning kernel is enqueued.  Does not block unless opt->validate is set.
+ */
+spkadd_status spkadd_plan(spkadd_handle** h, int k, const spkadd_csc* A, spkadd_dtype dtype, void* stream,
+                          const spkadd_options* opt);
+
+/*
+ * Symbolic phase: counts nnz(B(:,j)) for every column, scans them into B's
+ * column pointers (kept in the workspace) and writes the total nnz(B) to
+ * *nnz_B (host).  Blocks until the stream reaches that point.
+ */
+spkadd_status spkadd_symbolic(spkadd_handle* h, int64_t* nnz_B);
+
+/*
+ * Numeric phase: writes B.  All three are device memory the caller
+ * allocated from nnz_B:
+ *   B_col_ptr[n+1]   int64 (nnz(B) may exceed 2^31)
+ *   B_row_idx[nnz_B] int32, sorted ascending inside every column
+ *   B_val[nnz_B]     float or double per the plan's dtype
+ * Enqueued on the plan's stream; returns without blocking.  May be called
+ * again (with the same or other output buffers) to recompute B.
+ */
+spkadd_status spkadd_numeric(spkadd_handle* h, int64_t* B_col_ptr, int32_t* B_row_idx, void* B_val);
+
+/* Statistics of the handle (host out).  May synchronise the stream. */
+spkadd_status spkadd_get_info(spkadd_handle* h, spkadd_info* info);
+
+/* Frees the workspace (stream-ordered) and the handle.  NULL is accepted. */
+spkadd_status spkadd_destroy(spkadd_handle* h);
+
+/* Static, human-readable name of a status code. */
+const char* spkadd_status_string(spkadd_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int spkadd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPKADD_H */

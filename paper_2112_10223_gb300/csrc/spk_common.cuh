@@ -1,0 +1,201 @@
+// spk_common.cuh -- device helpers shared by the SpKAdd kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define SPK_FULL 0xffffffffu
+
+namespace spk {
+
+// ---------------------------------------------------------------------------
+// Work classes (Sec. III-A: columns are balanced by their summed input count).
+// ---------------------------------------------------------------------------
+enum : int32_t { CLS_EMPTY = 0, CLS_WARP = 1, CLS_CTA = 2, CLS_HEAVY = 3 };
+
+// Error bits in Counters::err (device side; the host maps them to statuses).
+enum : int32_t {
+  ERR_OVERFLOW = 1,      // a column's input count does not fit int32
+  ERR_UNSORTED = 2,      // validate: rows not strictly increasing in a column
+  ERR_RANGE = 4,         // validate: row outside [0, m) or bad col_ptr
+  ERR_WINDOW_CAP = 8,    // more row windows than the workspace holds
+  ERR_INTERNAL = 16,     // a size invariant failed (bug guard; work skipped)
+};
+
+// One thread-block work item of the numeric pass: a whole CTA-class column
+// or one row window of a heavy column (Alg. 8's B(r1:r2, j)).
+struct Window {
+  int32_t col;
+  int32_t r_lo, r_hi;   // rows [r_lo, r_hi)
+  int32_t u;            // distinct rows in the range (symbolic result)
+  int32_t out_off;      // first output slot of the range inside column col
+  int32_t search;       // -1: whole column; else row of the per-input offset table
+};
+
+struct Counters {
+  int32_t n_warp, n_cta, n_heavy;
+  int32_t n_windows;    // Window records appended
+  int32_t n_search;     // of those, split windows needing per-input offsets
+  int32_t n_ordered;    // warp columns the symbolic pass found evenly spread
+  int32_t err;
+  int32_t pad;
+};
+
+// Inputs as the kernels see them (device pointer tables of length k).
+struct Inputs {
+  const int32_t* const* cp;
+  const int32_t* const* ri;
+  const void* const* val;
+  int32_t k;
+  int32_t m;
+  int32_t n;
+  int32_t pad;
+  uint64_t home_mul;    // floor(2^48 / m): order-preserving home slot factor
+};
+
+// ---------------------------------------------------------------------------
+// Hash functions.  The paper hashes with (a * r) & (2^q - 1), a prime
+// (Sec. II-C).  The low q bits of a*r depend only on the low q bits of r, so
+// structured row sets (R-MAT) collide; we keep the prime multiplier and take
+// the high q bits of the 32-bit product instead (multiplicative hashing).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t hash_scrambled(int32_t r, int q) {
+  return (static_cast<uint32_t>(r) * 0x9E3779B1u) >> (32 - q);
+}
+
+// Order-preserving home slot: floor(r * 2^q / m) (computed as
+// (r * floor(2^48/m)) >> (48 - q)); monotone in r, always < 2^q.
+__device__ __forceinline__ uint32_t hash_ordered(int32_t r, uint64_t home_mul, int q) {
+  return static_cast<uint32_t>((static_cast<uint64_t>(static_cast<uint32_t>(r)) * home_mul) >> (48 - q));
+}
+
+__device__ __forceinline__ int ceil_log2(int x) {  // x >= 1
+  return x <= 1 ? 0 : 32 - __clz(x - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-level helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int warp_incl_scan(int x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(SPK_FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+__device__ __forceinline__ int warp_sum(int x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(SPK_FULL, x, o);
+  return x;
+}
+
+__device__ __forceinline__ int warp_max(int x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(SPK_FULL, x, o));
+  return x;
+}
+
+__device__ __forceinline__ int warp_min(int x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(SPK_FULL, x, o));
+  return x;
+}
+
+// ---------------------------------------------------------------------------
+// Segment walker.  A warp walks the concatenation of up to 32 segments (one
+// per lane: input `base + lane`, elements [beg, beg + len) of that input).
+// Flattened position e (0 <= e < total) belongs to segment
+// find(e) = max{ l : P_l <= e } where P is the exclusive prefix of lengths;
+// empty segments are skipped automatically.  The element's index inside its
+// input is e + delta(seg).  Consecutive positions of a warp round are
+// consecutive memory inside each segment, so loads stay coalesced.
+// ---------------------------------------------------------------------------
+struct SegWalk {
+  int P;      // this lane's segment start in the flattened order
+  int delta;  // beg - P
+  int total;  // sum of the 32 lengths
+
+  __device__ __forceinline__ void init(int beg, int len, int lane) {
+    int inc = warp_incl_scan(len, lane);
+    total = __shfl_sync(SPK_FULL, inc, 31);
+    P = inc - len;
+    delta = beg - P;
+  }
+  // Every lane of the warp must call this (it shuffles).
+  __device__ __forceinline__ int find(int e) const {
+    int idx = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+      int w = __shfl_sync(SPK_FULL, P, idx + step);
+      if (w <= e) idx += step;
+    }
+    return idx;
+  }
+  __device__ __forceinline__ int index_in_input(int e, int seg) const {
+    return e + __shfl_sync(SPK_FULL, delta, seg);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Block-level exclusive scan of one int per thread (BLOCK threads).
+// `tmp` must hold BLOCK/32 ints.  Returns the exclusive prefix; *total gets
+// the block sum.  Contains __syncthreads().
+// ---------------------------------------------------------------------------
+template <int BLOCK>
+__device__ __forceinline__ int block_excl_scan(int x, int* tmp, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = warp_incl_scan(x, lane);
+  if (lane == 31) tmp[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int v = lane < BLOCK / 32 ? tmp[lane] : 0;
+    int vi = warp_incl_scan(v, lane);
+    if (lane < BLOCK / 32) tmp[lane] = vi - v;
+    if (lane == 31) tmp[BLOCK / 32] = vi;  // needs BLOCK/32 + 1 slots
+  }
+  __syncthreads();
+  int r = tmp[wid] + inc - x;
+  *total = tmp[BLOCK / 32];
+  __syncthreads();
+  return r;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ int block_reduce_max(int x, int* tmp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  x = warp_max(x);
+  if (lane == 0) tmp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int v = lane < BLOCK / 32 ? tmp[lane] : INT32_MIN;
+    v = warp_max(v);
+    if (lane == 0) tmp[BLOCK / 32] = v;
+  }
+  __syncthreads();
+  int r = tmp[BLOCK / 32];
+  __syncthreads();
+  return r;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ int block_reduce_min(int x, int* tmp) {
+  return -block_reduce_max<BLOCK>(-x, tmp);
+}
+
+// Lower bound: first position p in [lo, hi) with a[p] >= key (hi if none).
+__device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, int lo, int hi, int32_t key) {
+  while (lo < hi) {
+    int mid = lo + ((hi - lo) >> 1);
+    if (__ldg(a + mid) < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Values: fp64 and fp32 shared-memory accumulation.
+template <typename V>
+__device__ __forceinline__ void smem_add(V* p, V v) { atomicAdd(p, v); }
+
+}  // namespace spk

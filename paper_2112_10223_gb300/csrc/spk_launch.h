@@ -1,0 +1,51 @@
+// spk_launch.h -- host-side launchers of the SpKAdd kernels (internal).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spk {
+
+struct Inputs;
+struct Counters;
+struct Window;
+
+// Per-launch limits shared by host and device code.
+constexpr int WARP_MAX_LIMIT = 512;     // warp class: s_j <= 512 -> table <= 1024 slots
+constexpr int CTA_MAX_LIMIT = 4096;     // CTA class: s_j <= 4096 -> table <= 8192 slots
+constexpr int WINDOW_MAX_LIMIT = 4096;  // numeric window: u <= 4096 -> table <= 8192 slots
+constexpr int SLAB_BITS = 20;           // heavy symbolic bitmap covers 2^20 rows per pass
+
+struct DeviceInfo {
+  int sms;
+  int smem_optin;  // max dynamic shared memory per block (opt-in)
+  int smem_per_sm;
+};
+
+cudaError_t launch_bin(const Inputs& in, int warp_max, int cta_max, int32_t* s, int32_t* u, int32_t* warp_list,
+                       int32_t* cta_list, int32_t* heavy_list, Counters* ctr, int sms, cudaStream_t st);
+cudaError_t launch_validate(const Inputs& in, const int64_t* nnz, Counters* ctr, int sms, cudaStream_t st);
+size_t scan_tiles(int64_t n);
+cudaError_t launch_scan(const int32_t* u, int n, long long* tile_buf, int64_t* col_ptr, cudaStream_t st);
+cudaError_t launch_window_search(const Inputs& in, const Window* win, const int32_t* search_list, int n_search,
+                                 int32_t* offs, int sms, cudaStream_t st);
+
+cudaError_t launch_sym_warp(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr,
+                            int32_t* u, uint8_t* mode, int warp_max, int sort_mode, Counters* ctr_w,
+                            const DeviceInfo& dev, cudaStream_t st);
+cudaError_t launch_sym_cta(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr, int32_t* u,
+                           Window* win, int64_t win_cap, Counters* ctr_w, int cta_max, const DeviceInfo& dev,
+                           cudaStream_t st);
+cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counters* ctr, int32_t* u, Window* win,
+                             int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
+                             const DeviceInfo& dev, cudaStream_t st);
+
+cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, int n_cols, const int32_t* u,
+                            const uint8_t* mode, const int64_t* col_ptr, int32_t* out_row, void* out_val,
+                            int warp_max, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
+cudaError_t launch_num_cta(const Inputs& in, bool f64, const Window* win, int n_win, const int32_t* offs,
+                           const int64_t* col_ptr, int32_t* out_row, void* out_val, int window_max,
+                           Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
+
+}  // namespace spk

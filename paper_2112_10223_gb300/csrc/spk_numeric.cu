@@ -1,0 +1,478 @@
+// spk_numeric.cu -- a4/a5 of the hot path: accumulate values and write each
+// output column sorted by row.
+//
+// Accumulation is Alg. 5 (HashAdd): an open-addressing table in shared memory
+// holding (row, value) pairs, empty = -1, linear probing, insert-or-add.  The
+// row key is claimed with atomicCAS and the value added with a shared-memory
+// atomicAdd, so the lanes of a warp insert concurrently.  Table size is a power
+// of two >= 2 nnz(B(:,j)) (from the symbolic pass).
+//
+// Sorting (the last step of Alg. 5) takes one of two forms:
+//   ordered  -- the table used the order-preserving home slot
+//               h(r) = floor(r * T / m).  Keys with a smaller home are smaller,
+//               and every key sits in the run of occupied slots that starts at
+//               its home.  With a histogram of homes (exclusive scan = number
+//               of keys with a smaller home), a key's output position is that
+//               prefix plus the number of smaller keys sharing its home, found
+//               by walking its run.  No data movement, no sort network.
+//   counting -- the table used the scrambled hash.  Occupied slots are
+//               compacted, bucketed by an order-preserving map of the row onto
+//               [rmin, rmax], placed by a counting sort, and ranked inside
+//               their bucket.
+// The symbolic pass chooses "ordered" per warp column (short probes); thread
+// block items always use "counting" (heavy columns are skewed).
+#include "spk_common.cuh"
+#include "spk_launch.h"
+
+namespace spk {
+
+__device__ __forceinline__ uint32_t get16(const uint32_t* c, uint32_t h) {
+  return (c[h >> 1] >> ((h & 1u) << 4)) & 0xffffu;
+}
+__device__ __forceinline__ uint32_t add16(uint32_t* c, uint32_t h) {  // returns the old 16-bit value
+  const uint32_t sh = (h & 1u) << 4;
+  return (atomicAdd(&c[h >> 1], 1u << sh) >> sh) & 0xffffu;
+}
+
+// Exclusive scan, by one warp, of n 16-bit counters packed two per word.
+__device__ __forceinline__ void warp_scan16(uint32_t* c, int n, int lane) {
+  const int nw = n >> 1;
+  const int per = (nw + 31) >> 5;
+  const int w0 = lane * per;
+  int loc = 0;
+  for (int t = 0; t < per; ++t)
+    if (w0 + t < nw) {
+      const uint32_t x = c[w0 + t];
+      loc += (int)(x & 0xffffu) + (int)(x >> 16);
+    }
+  int run = warp_incl_scan(loc, lane) - loc;
+  for (int t = 0; t < per; ++t)
+    if (w0 + t < nw) {
+      const uint32_t x = c[w0 + t];
+      const int lo = (int)(x & 0xffffu), hi = (int)(x >> 16);
+      c[w0 + t] = (uint32_t)run | ((uint32_t)(run + lo) << 16);
+      run += lo + hi;
+    }
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void block_scan16(uint32_t* c, int n, int* red) {
+  const int nw = n >> 1;
+  const int per = (nw + BLOCK - 1) / BLOCK;
+  const int w0 = threadIdx.x * per;
+  int loc = 0;
+  for (int t = 0; t < per; ++t)
+    if (w0 + t < nw) {
+      const uint32_t x = c[w0 + t];
+      loc += (int)(x & 0xffffu) + (int)(x >> 16);
+    }
+  int total;
+  int run = block_excl_scan<BLOCK>(loc, red, &total);
+  for (int t = 0; t < per; ++t)
+    if (w0 + t < nw) {
+      const uint32_t x = c[w0 + t];
+      const int lo = (int)(x & 0xffffu), hi = (int)(x >> 16);
+      c[w0 + t] = (uint32_t)run | ((uint32_t)(run + lo) << 16);
+      run += lo + hi;
+    }
+}
+
+// Order-preserving bucket of row r on [rmin, rmin + span): floor((r-rmin)*NB/span).
+__device__ __forceinline__ uint32_t bucket_of(int32_t r, int32_t rmin, uint64_t bmul) {
+  return (uint32_t)(((uint64_t)(uint32_t)(r - rmin) * bmul) >> 32);
+}
+
+template <typename V>
+__device__ __forceinline__ const V* val_ptr(const Inputs& in, int i) {
+  return static_cast<const V*>(in.val[i]);
+}
+
+// Insert-or-add of (r, v) into the table (Alg. 5, inner loop).  Returns the
+// slot, or -1 when every slot holds another key (only possible if the inputs
+// changed after the symbolic pass; the probe count is bounded either way).
+__device__ __forceinline__ int table_insert(int32_t* keys, uint32_t h, uint32_t mask, int32_t r, bool& fresh) {
+  fresh = false;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int old = atomicCAS(&keys[h], -1, r);
+    if (old == -1) {
+      fresh = true;
+      return (int)h;
+    }
+    if (old == r) return (int)h;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+template <typename V, int WARPS, int U>
+__global__ void __launch_bounds__(WARPS * 32) k_num_warp(Inputs in, const int32_t* __restrict__ list, int ncols,
+                                                         const int32_t* __restrict__ u_arr,
+                                                         const uint8_t* __restrict__ mode,
+                                                         const int64_t* __restrict__ col_ptr,
+                                                         int32_t* __restrict__ out_row, V* __restrict__ out_val,
+                                                         int tmax, Counters* ctr_w) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char* base = sm_raw + (size_t)wid * tmax * (sizeof(V) + 6);
+  V* vals = reinterpret_cast<V*>(base);
+  int32_t* keys = reinterpret_cast<int32_t*>(vals + tmax);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(keys + tmax);  // tmax 16-bit counters
+  for (int c = blockIdx.x * WARPS + wid; c < ncols; c += gridDim.x * WARPS) {
+    const int j = list[c];
+    const int u = u_arr[j];
+    const bool ordered = mode[j] != 0;
+    const int64_t out = col_ptr[j];
+    const int q = max(6, ceil_log2(2 * u));
+    const int T = 1 << q;
+    if (T > tmax) continue;  // not reachable for a warp-class column
+    const uint32_t mask = (uint32_t)T - 1u;
+    for (int p = lane; p < T; p += 32) {
+      keys[p] = -1;
+      vals[p] = V(0);
+    }
+    for (int p = lane; p < T / 2; p += 32) cnt[p] = 0u;
+    __syncwarp();
+    int rmin = INT32_MAX, rmax = -1;
+    int nfresh = 0;
+    bool full = false;
+    for (int cb = 0; cb < in.k; cb += 32) {
+      const int i = cb + lane;
+      int beg = 0, len = 0;
+      if (i < in.k) {
+        const int32_t* cp = in.cp[i];
+        beg = __ldg(cp + j);
+        len = __ldg(cp + j + 1) - beg;
+      }
+      SegWalk w;
+      w.init(beg, len, lane);
+      for (int e0 = 0; e0 < w.total; e0 += 32 * U) {
+        int32_t r[U];
+        V v[U];
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+          const int e = e0 + t * 32 + lane;
+          const int seg = w.find(e);
+          const int idx = w.index_in_input(e, seg);
+          r[t] = -1;
+          v[t] = V(0);
+          if (e < w.total) {
+            r[t] = __ldg(in.ri[cb + seg] + idx);
+            v[t] = __ldg(val_ptr<V>(in, cb + seg) + idx);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+          if (r[t] < 0) continue;
+          bool fresh;
+          if (ordered) {
+            const uint32_t home = hash_ordered(r[t], in.home_mul, q) & mask;
+            const int h = table_insert(keys, home, mask, r[t], fresh);
+            if (h < 0) {
+              full = true;
+              continue;
+            }
+            if (fresh) add16(cnt, home);
+            atomicAdd(&vals[h], v[t]);
+          } else {
+            const int h = table_insert(keys, hash_scrambled(r[t], q), mask, r[t], fresh);
+            if (h < 0) {
+              full = true;
+              continue;
+            }
+            atomicAdd(&vals[h], v[t]);
+            rmin = min(rmin, r[t]);
+            rmax = max(rmax, r[t]);
+          }
+          nfresh += fresh;
+        }
+      }
+    }
+    __syncwarp();
+    // The distinct-row count must equal the symbolic result, or the output
+    // slots of this column would not match col_ptr: report and skip.
+    if (__any_sync(SPK_FULL, full) || warp_sum(nfresh) != u) {
+      if (lane == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
+      continue;
+    }
+    if (ordered) {
+      warp_scan16(cnt, T, lane);
+      __syncwarp();
+      for (int p = lane; p < T; p += 32) {
+        const int32_t key = keys[p];
+        if (key < 0) continue;
+        const uint32_t home = hash_ordered(key, in.home_mul, q) & mask;
+        const int b = (int)get16(cnt, home);
+        const int e = (home + 1u < (uint32_t)T) ? (int)get16(cnt, home + 1u) : u;
+        int rank = b;
+        if (e - b > 1) {
+          for (uint32_t qq = home;; qq = (qq + 1u) & mask) {
+            const int32_t kq = keys[qq];
+            if (kq < 0) break;
+            if (kq < key && (hash_ordered(kq, in.home_mul, q) & mask) == home) ++rank;
+          }
+        }
+        out_row[out + rank] = key;
+        out_val[out + rank] = vals[p];
+      }
+    } else {
+      rmin = warp_min(rmin);
+      rmax = warp_max(rmax);
+      // Compact occupied slots into [0, u) (chunks are read before being overwritten).
+      int wpos = 0;
+      for (int p0 = 0; p0 < T; p0 += 32) {
+        const int32_t key = keys[p0 + lane];
+        const V val = vals[p0 + lane];
+        const unsigned bal = __ballot_sync(SPK_FULL, key >= 0);
+        __syncwarp();
+        if (key >= 0) {
+          const int d = wpos + __popc(bal & ((1u << lane) - 1u));
+          keys[d] = key;
+          vals[d] = val;
+        }
+        wpos += __popc(bal);
+        __syncwarp();
+      }
+      // Counting sort by bucket into the staging half [NB, NB + u).
+      const int NB = T / 2;
+      const uint32_t span = (uint32_t)(rmax - rmin) + 1u;
+      const uint64_t bmul = ((uint64_t)NB << 32) / span;
+      for (int x = lane; x < u; x += 32) add16(cnt, bucket_of(keys[x], rmin, bmul));
+      __syncwarp();
+      warp_scan16(cnt, NB, lane);
+      __syncwarp();
+      for (int x = lane; x < u; x += 32) {
+        const int32_t key = keys[x];
+        const int pos = (int)add16(cnt, bucket_of(key, rmin, bmul));
+        keys[NB + pos] = key;
+        vals[NB + pos] = vals[x];
+      }
+      __syncwarp();
+      for (int x = lane; x < u; x += 32) {
+        const int32_t key = keys[NB + x];
+        const uint32_t b = bucket_of(key, rmin, bmul);
+        const int lo = b ? (int)get16(cnt, b - 1u) : 0;
+        const int hi = (int)get16(cnt, b);
+        int rank = lo;
+        for (int y = lo; y < hi; ++y) rank += keys[NB + y] < key;
+        out_row[out + rank] = key;
+        out_val[out + rank] = vals[NB + x];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// One thread block per work item: a CTA-class column or a heavy column's row
+// window (Alg. 8: B(r1:r2, j) <- HashAdd(A_1(r1:r2, j), ..., A_k(r1:r2, j))).
+template <typename V, int BLOCK, int U, int SMAX>
+__global__ void __launch_bounds__(BLOCK) k_num_cta(Inputs in, const Window* __restrict__ win, int nwin,
+                                                   const int32_t* __restrict__ offs,
+                                                   const int64_t* __restrict__ col_ptr,
+                                                   int32_t* __restrict__ out_row, V* __restrict__ out_val, int tmax,
+                                                   Counters* ctr_w) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ int red[BLOCK / 32 + 1];
+  constexpr int NW = BLOCK / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  V* vals = reinterpret_cast<V*>(sm_raw);
+  int32_t* keys = reinterpret_cast<int32_t*>(vals + tmax);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(keys + tmax);  // tmax/2 16-bit counters
+  for (int wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
+    const Window W = win[wi];
+    const int u = W.u;
+    const int j = W.col;
+    const int64_t out = col_ptr[j] + W.out_off;
+    const int q = max(6, ceil_log2(2 * u));
+    const int T = 1 << q;
+    if (T > tmax || T / BLOCK > SMAX) {
+      if (threadIdx.x == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
+      continue;
+    }
+    const uint32_t mask = (uint32_t)T - 1u;
+    for (int p = threadIdx.x; p < T; p += BLOCK) {
+      keys[p] = -1;
+      vals[p] = V(0);
+    }
+    for (int p = threadIdx.x; p < T / 4; p += BLOCK) cnt[p] = 0u;
+    __syncthreads();
+    int rmin = INT32_MAX, rmax = -1;
+    for (int cb = 0; cb < in.k; cb += 32) {
+      const int i = cb + lane;
+      int beg = 0, len = 0;
+      if (i < in.k) {
+        if (W.search < 0) {
+          const int32_t* cp = in.cp[i];
+          beg = __ldg(cp + j);
+          len = __ldg(cp + j + 1) - beg;
+        } else {
+          const int32_t* o = offs + ((int64_t)W.search * in.k + i) * 2;
+          beg = o[0];
+          len = o[1] - beg;
+        }
+      }
+      SegWalk w;
+      w.init(beg, len, lane);
+      for (int e0 = wid * 32 * U; e0 < w.total; e0 += NW * 32 * U) {
+        int32_t r[U];
+        V v[U];
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+          const int e = e0 + t * 32 + lane;
+          const int seg = w.find(e);
+          const int idx = w.index_in_input(e, seg);
+          r[t] = -1;
+          v[t] = V(0);
+          if (e < w.total) {
+            r[t] = __ldg(in.ri[cb + seg] + idx);
+            v[t] = __ldg(val_ptr<V>(in, cb + seg) + idx);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+          if (r[t] < 0) continue;
+          bool fresh;
+          const int h = table_insert(keys, hash_scrambled(r[t], q), mask, r[t], fresh);
+          if (h < 0) continue;  // table full: the count check below reports it
+          atomicAdd(&vals[h], v[t]);
+          rmin = min(rmin, r[t]);
+          rmax = max(rmax, r[t]);
+        }
+      }
+    }
+    __syncthreads();
+    rmin = block_reduce_min<BLOCK>(rmin, red);
+    rmax = block_reduce_max<BLOCK>(rmax, red);
+    // Compaction through registers: thread t owns slots [t*S, t*S + S).
+    const int S = T >= BLOCK ? T / BLOCK : 1;
+    const int p0 = threadIdx.x * S;
+    int32_t kk[SMAX];
+    V vv[SMAX];
+    int mine = 0;
+#pragma unroll
+    for (int t = 0; t < SMAX; ++t) {
+      kk[t] = -1;
+      vv[t] = V(0);
+      if (t < S && p0 + t < T) {
+        kk[t] = keys[p0 + t];
+        vv[t] = vals[p0 + t];
+        mine += kk[t] >= 0;
+      }
+    }
+    int tot;
+    int dst = block_excl_scan<BLOCK>(mine, red, &tot);  // synchronises: all reads are done
+    const bool ok = (tot == u);
+    if (ok) {
+#pragma unroll
+      for (int t = 0; t < SMAX; ++t)
+        if (kk[t] >= 0) {
+          keys[dst] = kk[t];
+          vals[dst] = vv[t];
+          ++dst;
+        }
+    } else if (threadIdx.x == 0) {
+      atomicOr(&ctr_w->err, ERR_INTERNAL);
+    }
+    __syncthreads();
+    if (!ok) continue;
+    const int NB = T / 2;
+    const uint32_t span = (uint32_t)(rmax - rmin) + 1u;
+    const uint64_t bmul = ((uint64_t)NB << 32) / span;
+    for (int x = threadIdx.x; x < u; x += BLOCK) add16(cnt, bucket_of(keys[x], rmin, bmul));
+    __syncthreads();
+    block_scan16<BLOCK>(cnt, NB, red);
+    __syncthreads();
+    for (int x = threadIdx.x; x < u; x += BLOCK) {
+      const int32_t key = keys[x];
+      const int pos = (int)add16(cnt, bucket_of(key, rmin, bmul));
+      keys[NB + pos] = key;
+      vals[NB + pos] = vals[x];
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < u; x += BLOCK) {
+      const int32_t key = keys[NB + x];
+      const uint32_t b = bucket_of(key, rmin, bmul);
+      const int lo = b ? (int)get16(cnt, b - 1u) : 0;
+      const int hi = (int)get16(cnt, b);
+      int rank = lo;
+      for (int y = lo; y < hi; ++y) rank += keys[NB + y] < key;
+      out_row[out + rank] = key;
+      out_val[out + rank] = vals[NB + x];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+static int pow2_at_least(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+static int blocks_per_sm(const DeviceInfo& dev, size_t smem_per_block, int threads_per_block) {
+  const size_t reserve = 1024;
+  int b = (int)(dev.smem_per_sm / (smem_per_block + reserve));
+  int bt = 2048 / threads_per_block;
+  if (b > bt) b = bt;
+  if (b > 32) b = 32;
+  return b < 1 ? 1 : b;
+}
+
+template <typename V>
+static cudaError_t launch_num_warp_t(const Inputs& in, const int32_t* list, int n_cols, const int32_t* u,
+                                     const uint8_t* mode, const int64_t* col_ptr, int32_t* out_row, void* out_val,
+                                     int warp_max, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+  constexpr int WARPS = 8;
+  const int tmax = pow2_at_least(2 * warp_max) < 64 ? 64 : pow2_at_least(2 * warp_max);
+  const size_t smem = (size_t)WARPS * tmax * (sizeof(V) + 6);
+  auto kern = k_num_warp<V, WARPS, 4>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int grid = dev.sms * blocks_per_sm(dev, smem, WARPS * 32);
+  const int need = (n_cols + WARPS - 1) / WARPS;
+  if (grid > need) grid = need;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, WARPS * 32, smem, st>>>(in, list, n_cols, u, mode, col_ptr, out_row, static_cast<V*>(out_val), tmax,
+                                       ctr_w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, int n_cols, const int32_t* u,
+                            const uint8_t* mode, const int64_t* col_ptr, int32_t* out_row, void* out_val,
+                            int warp_max, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+  if (n_cols <= 0) return cudaSuccess;
+  return f64 ? launch_num_warp_t<double>(in, list, n_cols, u, mode, col_ptr, out_row, out_val, warp_max, ctr_w, dev,
+                                         st)
+             : launch_num_warp_t<float>(in, list, n_cols, u, mode, col_ptr, out_row, out_val, warp_max, ctr_w, dev,
+                                        st);
+}
+
+template <typename V>
+static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_win, const int32_t* offs,
+                                    const int64_t* col_ptr, int32_t* out_row, void* out_val, int window_max,
+                                    Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+  constexpr int BLOCK = 512;
+  constexpr int SMAX = 2 * WINDOW_MAX_LIMIT / BLOCK;  // 16 slots per thread at the largest table
+  const int tmax = pow2_at_least(2 * window_max);
+  const size_t smem = (size_t)tmax * (sizeof(V) + 4) + (size_t)tmax / 2 * 2;
+  auto kern = k_num_cta<V, BLOCK, 4, SMAX>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int grid = dev.sms * blocks_per_sm(dev, smem, BLOCK);
+  if (grid > n_win) grid = n_win;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, BLOCK, smem, st>>>(in, win, n_win, offs, col_ptr, out_row, static_cast<V*>(out_val), tmax, ctr_w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_num_cta(const Inputs& in, bool f64, const Window* win, int n_win, const int32_t* offs,
+                           const int64_t* col_ptr, int32_t* out_row, void* out_val, int window_max,
+                           Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+  if (n_win <= 0) return cudaSuccess;
+  return f64 ? launch_num_cta_t<double>(in, win, n_win, offs, col_ptr, out_row, out_val, window_max, ctr_w, dev, st)
+             : launch_num_cta_t<float>(in, win, n_win, offs, col_ptr, out_row, out_val, window_max, ctr_w, dev, st);
+}
+
+}  // namespace spk

@@ -1,0 +1,240 @@
+// spk_plan.cu -- column binning, input validation, the column-pointer scan
+// and the per-input offsets of heavy-column row windows.
+#include "spk_common.cuh"
+#include "spk_launch.h"
+
+namespace spk {
+
+// Appends `value` to `list` for every lane with pred set; one atomic per warp.
+// All 32 lanes must be active.
+__device__ __forceinline__ void warp_append(bool pred, int32_t* __restrict__ list, int32_t* counter, int32_t value,
+                                            int lane) {
+  const unsigned m = __ballot_sync(SPK_FULL, pred);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(SPK_FULL, base, leader);
+  if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+// a1 of the hot path: s_j = sum_i nnz(A_i(:,j)) and the column's class
+// (Sec. III-A: the symbolic phase balances load on the summed input count).
+__global__ void __launch_bounds__(256) k_bin(Inputs in, int warp_max, int cta_max, int32_t* __restrict__ s_out,
+                                             int32_t* __restrict__ u_out, int32_t* __restrict__ warp_list,
+                                             int32_t* __restrict__ cta_list, int32_t* __restrict__ heavy_list,
+                                             Counters* __restrict__ ctr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < in.n; j0 += stride) {
+    const int j = (int)(j0 + threadIdx.x);
+    const bool live = j < in.n;
+    int64_t s = 0;
+    if (live) {
+      for (int i = 0; i < in.k; ++i) {
+        const int32_t* cp = in.cp[i];
+        s += (int64_t)__ldg(cp + j + 1) - (int64_t)__ldg(cp + j);
+      }
+    }
+    int cls = CLS_EMPTY;
+    if (live) {
+      if (s > INT32_MAX) {
+        atomicOr(&ctr->err, ERR_OVERFLOW);
+        s = INT32_MAX;
+      }
+      if (s <= 0) cls = CLS_EMPTY;
+      else if (s <= warp_max) cls = CLS_WARP;
+      else if (s <= cta_max) cls = CLS_CTA;
+      else cls = CLS_HEAVY;
+      s_out[j] = (int32_t)s;
+      if (cls == CLS_EMPTY) u_out[j] = 0;
+    }
+    warp_append(cls == CLS_WARP, warp_list, &ctr->n_warp, j, lane);
+    warp_append(cls == CLS_CTA, cta_list, &ctr->n_cta, j, lane);
+    warp_append(cls == CLS_HEAVY, heavy_list, &ctr->n_heavy, j, lane);
+  }
+}
+
+// Optional input check: col_ptr[0] = 0, non-decreasing, col_ptr[n] = nnz;
+// rows in [0, m) and strictly increasing inside each column.
+__global__ void __launch_bounds__(256) k_validate(Inputs in, const int64_t* __restrict__ nnz, Counters* ctr) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int err = 0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < in.n; j += stride) {
+    for (int i = 0; i < in.k; ++i) {
+      const int32_t* cp = in.cp[i];
+      const int64_t b = __ldg(cp + j), e = __ldg(cp + j + 1);
+      if (j == 0 && b != 0) err |= ERR_RANGE;
+      if (j == in.n - 1 && e != nnz[i]) err |= ERR_RANGE;
+      if (b < 0 || e < b || e > nnz[i]) {
+        err |= ERR_RANGE;
+        continue;
+      }
+      const int32_t* ri = in.ri[i];
+      int32_t prev = -1;
+      for (int64_t p = b; p < e; ++p) {
+        const int32_t r = __ldg(ri + p);
+        if (r < 0 || r >= in.m) err |= ERR_RANGE;
+        if (r <= prev) err |= ERR_UNSORTED;
+        prev = r;
+      }
+    }
+  }
+  if (err) atomicOr(&ctr->err, err);
+}
+
+// ---------------------------------------------------------------------------
+// a3: col_ptr_B = exclusive scan of u (int32 counts -> int64 pointers).
+// Three passes: tile sums, scan of the tile sums, per-tile scan.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_BLOCK = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+__device__ __forceinline__ long long warp_incl_scan64(long long x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(SPK_FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Block-wide exclusive scan of 64-bit values; tmp holds 33 entries.
+__device__ __forceinline__ long long block_excl_scan64(long long x, long long* tmp, long long* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long inc = warp_incl_scan64(x, lane);
+  if (lane == 31) tmp[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    long long v = lane < SCAN_BLOCK / 32 ? tmp[lane] : 0;
+    long long vi = warp_incl_scan64(v, lane);
+    if (lane < SCAN_BLOCK / 32) tmp[lane] = vi - v;
+    if (lane == 31) tmp[32] = vi;
+  }
+  __syncthreads();
+  long long r = tmp[wid] + inc - x;
+  *total = tmp[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_tiles(const int32_t* __restrict__ u, int n,
+                                                          long long* __restrict__ tile_sum) {
+  __shared__ long long tmp[33];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  long long acc = 0;
+#pragma unroll
+  for (int t = 0; t < SCAN_ITEMS; ++t) {
+    const int64_t j = base + (int64_t)t * SCAN_BLOCK + threadIdx.x;
+    if (j < n) acc += u[j];
+  }
+  long long total;
+  block_excl_scan64(acc, tmp, &total);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_sums(long long* __restrict__ tile_sum, int tiles,
+                                                         long long* __restrict__ grand_total) {
+  __shared__ long long tmp[33];
+  long long carry = 0;
+  for (int b = 0; b < tiles; b += SCAN_BLOCK) {
+    const int t = b + threadIdx.x;
+    long long v = t < tiles ? tile_sum[t] : 0;
+    long long total;
+    long long ex = block_excl_scan64(v, tmp, &total);
+    if (t < tiles) tile_sum[t] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) *grand_total = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_apply(const int32_t* __restrict__ u, int n,
+                                                          const long long* __restrict__ tile_off,
+                                                          const long long* __restrict__ grand_total,
+                                                          int64_t* __restrict__ col_ptr) {
+  __shared__ long long tmp[33];
+  // Each thread owns SCAN_ITEMS consecutive counts of the tile.
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int32_t v[SCAN_ITEMS];
+  long long acc = 0;
+#pragma unroll
+  for (int t = 0; t < SCAN_ITEMS; ++t) {
+    const int64_t j = base + t;
+    v[t] = j < n ? u[j] : 0;
+    acc += v[t];
+  }
+  long long total;
+  long long run = block_excl_scan64(acc, tmp, &total) + tile_off[blockIdx.x];
+#pragma unroll
+  for (int t = 0; t < SCAN_ITEMS; ++t) {
+    const int64_t j = base + t;
+    if (j < n) col_ptr[j] = run;
+    run += v[t];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) col_ptr[n] = *grand_total;
+}
+
+// Per-input offsets of split row windows (Sec. III-B: "partition rows ...
+// using binary searches"): for window w and input i, the first entry of
+// A_i(:,col) with row >= r_lo and the first with row >= r_hi.
+__global__ void __launch_bounds__(256) k_window_search(Inputs in, const Window* __restrict__ win,
+                                                       const int32_t* __restrict__ search_list, int n_search,
+                                                       int32_t* __restrict__ offs) {
+  const int64_t total = (int64_t)n_search * in.k;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int s = (int)(t / in.k), i = (int)(t - (int64_t)s * in.k);
+    const Window w = win[search_list[s]];
+    const int32_t* cp = in.cp[i];
+    const int b = __ldg(cp + w.col), e = __ldg(cp + w.col + 1);
+    const int32_t* ri = in.ri[i];
+    const int lo = lower_bound_i32(ri, b, e, w.r_lo);
+    const int hi = lower_bound_i32(ri, lo, e, w.r_hi);
+    offs[2 * t] = lo;
+    offs[2 * t + 1] = hi;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+cudaError_t launch_bin(const Inputs& in, int warp_max, int cta_max, int32_t* s, int32_t* u, int32_t* wl, int32_t* cl,
+                       int32_t* hl, Counters* ctr, int sms, cudaStream_t st) {
+  if (in.n == 0) return cudaSuccess;
+  int64_t blocks = ((int64_t)in.n + 255) / 256;
+  if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+  k_bin<<<(int)blocks, 256, 0, st>>>(in, warp_max, cta_max, s, u, wl, cl, hl, ctr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const Inputs& in, const int64_t* nnz, Counters* ctr, int sms, cudaStream_t st) {
+  if (in.n == 0) return cudaSuccess;
+  int64_t blocks = ((int64_t)in.n + 255) / 256;
+  if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+  k_validate<<<(int)blocks, 256, 0, st>>>(in, nnz, ctr);
+  return cudaGetLastError();
+}
+
+size_t scan_tiles(int64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 1; }
+
+cudaError_t launch_scan(const int32_t* u, int n, long long* tile_buf, int64_t* col_ptr, cudaStream_t st) {
+  const int tiles = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
+  long long* grand = tile_buf + tiles;
+  if (tiles > 0) k_scan_tiles<<<tiles, SCAN_BLOCK, 0, st>>>(u, n, tile_buf);
+  k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(tile_buf, tiles, grand);
+  k_scan_apply<<<tiles > 0 ? tiles : 1, SCAN_BLOCK, 0, st>>>(u, n, tile_buf, grand, col_ptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_search(const Inputs& in, const Window* win, const int32_t* search_list, int n_search,
+                                 int32_t* offs, int sms, cudaStream_t st) {
+  if (n_search <= 0) return cudaSuccess;
+  int64_t total = (int64_t)n_search * in.k;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > (int64_t)sms * 32) blocks = (int64_t)sms * 32;
+  k_window_search<<<(int)blocks, 256, 0, st>>>(in, win, search_list, n_search, offs);
+  return cudaGetLastError();
+}
+
+}  // namespace spk

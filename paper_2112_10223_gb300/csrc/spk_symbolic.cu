@@ -1,0 +1,363 @@
+// spk_symbolic.cu -- a2 of the hot path: nnz(B(:,j)) per column.
+//
+// Warp class (s_j <= warp_max): one warp per column, a shared-memory
+//   open-addressing table of keys only (Alg. 6 HashSymbolic), size a power of
+//   two >= 2 s_j, linear probing, atomicCAS on the row key.  The table first
+//   tries an order-preserving home slot floor(r * T / m); a column whose
+//   longest probe stays short is marked "ordered" for the numeric pass, which
+//   then gets the sorted output from the table layout instead of a sort.
+// CTA class (s_j <= cta_max): one thread block per column, same table with the
+//   scrambled (multiplicative) hash.  Emits one numeric work item per column.
+// Heavy class: one thread block per column with a shared-memory bitmap of a
+//   2^20-row slab (the dense-accumulator form of the symbolic step, which
+//   Sec. II-D allows in place of the hash).  Popcounts give nnz(B(:,j)) and
+//   cut the column into row windows of at most window_max distinct rows each
+//   (Alg. 7/8's sliding windows, sized to shared memory and balanced by count
+//   rather than by equal row ranges).
+#include "spk_common.cuh"
+#include "spk_launch.h"
+
+namespace spk {
+
+constexpr int PROBE_CAP = 32;  // longest probe an "ordered" warp column may need
+
+template <int WARPS, int U>
+__global__ void __launch_bounds__(WARPS * 32) k_sym_warp(Inputs in, const int32_t* __restrict__ list,
+                                                         const int32_t* __restrict__ s_arr,
+                                                         const Counters* __restrict__ ctr,
+                                                         int32_t* __restrict__ u_out, uint8_t* __restrict__ mode_out,
+                                                         int tmax, int try_ordered, Counters* ctr_w) {
+  extern __shared__ int32_t sm_keys[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* keys = sm_keys + wid * tmax;
+  const int ncols = ctr->n_warp;
+  int n_ord = 0;
+  for (int c = blockIdx.x * WARPS + wid; c < ncols; c += gridDim.x * WARPS) {
+    const int j = list[c];
+    const int s = s_arr[j];
+    const int q = max(6, ceil_log2(2 * s));
+    const int T = 1 << q;
+    if (T > tmax) {  // cannot happen for a warp-class column; guard the shared table
+      if (lane == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
+      continue;
+    }
+    for (int p = lane; p < T; p += 32) keys[p] = -1;
+    __syncwarp();
+    int newc = 0, maxp = 0;
+    for (int cb = 0; cb < in.k; cb += 32) {
+      const int i = cb + lane;
+      int beg = 0, len = 0;
+      if (i < in.k) {
+        const int32_t* cp = in.cp[i];
+        beg = __ldg(cp + j);
+        len = __ldg(cp + j + 1) - beg;
+      }
+      SegWalk w;
+      w.init(beg, len, lane);
+      for (int e0 = 0; e0 < w.total; e0 += 32 * U) {
+        int32_t r[U];
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+          const int e = e0 + t * 32 + lane;
+          const int seg = w.find(e);
+          const int idx = w.index_in_input(e, seg);
+          r[t] = -1;
+          if (e < w.total) r[t] = __ldg(in.ri[cb + seg] + idx);
+        }
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+          if (r[t] < 0) continue;
+          uint32_t h = (try_ordered ? hash_ordered(r[t], in.home_mul, q) : hash_scrambled(r[t], q)) & (T - 1);
+          int probes = 0;
+          for (; probes < T; ++probes) {  // T > s_j keys: an empty slot is always found
+            const int old = atomicCAS(&keys[h], -1, r[t]);
+            if (old == -1) {
+              ++newc;
+              break;
+            }
+            if (old == r[t]) break;
+            h = (h + 1) & (T - 1);
+          }
+          maxp = max(maxp, probes);
+        }
+      }
+    }
+    newc = warp_sum(newc);
+    maxp = warp_max(maxp);
+    if (lane == 0) {
+      u_out[j] = newc;
+      const int ord = (try_ordered && maxp <= PROBE_CAP) ? 1 : 0;
+      mode_out[j] = (uint8_t)ord;
+      n_ord += ord;
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && n_ord) atomicAdd(&ctr_w->n_ordered, n_ord);
+}
+
+template <int BLOCK, int U>
+__global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __restrict__ list,
+                                                   const int32_t* __restrict__ s_arr, const Counters* __restrict__ ctr,
+                                                   int32_t* __restrict__ u_out, Window* __restrict__ win,
+                                                   int64_t win_cap, int tmax, Counters* ctr_w) {
+  extern __shared__ int32_t keys[];
+  __shared__ int red[BLOCK / 32 + 1];
+  constexpr int NW = BLOCK / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ncols = ctr->n_cta;
+  for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
+    const int j = list[c];
+    const int s = s_arr[j];
+    const int q = max(6, ceil_log2(2 * s));
+    const int T = 1 << q;
+    if (T > tmax) {
+      if (threadIdx.x == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
+      continue;
+    }
+    for (int p = threadIdx.x; p < T; p += BLOCK) keys[p] = -1;
+    __syncthreads();
+    int newc = 0;
+    for (int cb = 0; cb < in.k; cb += 32) {
+      const int i = cb + lane;
+      int beg = 0, len = 0;
+      if (i < in.k) {
+        const int32_t* cp = in.cp[i];
+        beg = __ldg(cp + j);
+        len = __ldg(cp + j + 1) - beg;
+      }
+      SegWalk w;
+      w.init(beg, len, lane);
+      for (int e0 = wid * 32 * U; e0 < w.total; e0 += NW * 32 * U) {
+        int32_t r[U];
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+          const int e = e0 + t * 32 + lane;
+          const int seg = w.find(e);
+          const int idx = w.index_in_input(e, seg);
+          r[t] = -1;
+          if (e < w.total) r[t] = __ldg(in.ri[cb + seg] + idx);
+        }
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+          if (r[t] < 0) continue;
+          uint32_t h = hash_scrambled(r[t], q);
+          for (int probes = 0; probes < T; ++probes) {  // T > s_j keys: an empty slot is always found
+            const int old = atomicCAS(&keys[h], -1, r[t]);
+            if (old == -1) {
+              ++newc;
+              break;
+            }
+            if (old == r[t]) break;
+            h = (h + 1) & (T - 1);
+          }
+        }
+      }
+    }
+    int total;
+    block_excl_scan<BLOCK>(newc, red, &total);
+    if (threadIdx.x == 0) {
+      u_out[j] = total;
+      const int wi = atomicAdd(&ctr_w->n_windows, 1);
+      if (wi < win_cap) {
+        Window w;
+        w.col = j;
+        w.r_lo = 0;
+        w.r_hi = in.m;
+        w.u = total;
+        w.out_off = 0;
+        w.search = -1;
+        win[wi] = w;
+      } else {
+        atomicOr(&ctr_w->err, ERR_WINDOW_CAP);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int HEAVY_BLOCK = 1024;
+constexpr int MAX_SLAB_WINDOWS = 1100;  // (2^20 rows / 32 bits per word) / (1024 - 32) + 2
+
+template <int BLOCK, int U>
+__global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* __restrict__ list,
+                                                     const Counters* __restrict__ ctr, int32_t* __restrict__ u_out,
+                                                     Window* __restrict__ win, int32_t* __restrict__ search_list,
+                                                     int64_t win_cap, int win_target, int slab_words,
+                                                     Counters* ctr_w) {
+  extern __shared__ uint32_t bm[];
+  __shared__ int red[BLOCK / 32 + 1];
+  __shared__ int bnd[MAX_SLAB_WINDOWS + 1];
+  __shared__ int cval[MAX_SLAB_WINDOWS + 1];
+  __shared__ int s_col_u, s_wbase, s_sbase;
+  constexpr int NW = BLOCK / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ncols = ctr->n_heavy;
+  const int slab_rows = slab_words * 32;
+  const int nslabs = (int)(((int64_t)in.m + slab_rows - 1) / slab_rows);
+  for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
+    const int j = list[c];
+    if (threadIdx.x == 0) s_col_u = 0;
+    for (int slab = 0; slab < nslabs; ++slab) {
+      const int lo = slab * slab_rows;
+      const int hi = (int)min((int64_t)in.m, (int64_t)lo + slab_rows);
+      const int words = (hi - lo + 31) >> 5;
+      for (int p = threadIdx.x; p < words; p += BLOCK) bm[p] = 0u;
+      __syncthreads();
+      for (int cb = 0; cb < in.k; cb += 32) {
+        const int i = cb + lane;
+        int beg = 0, len = 0;
+        if (i < in.k) {
+          const int32_t* cp = in.cp[i];
+          int b = __ldg(cp + j), e = __ldg(cp + j + 1);
+          if (nslabs > 1) {
+            const int32_t* ri = in.ri[i];
+            b = lower_bound_i32(ri, b, e, lo);
+            e = lower_bound_i32(ri, b, e, hi);
+          }
+          beg = b;
+          len = e - b;
+        }
+        SegWalk w;
+        w.init(beg, len, lane);
+        for (int e0 = wid * 32 * U; e0 < w.total; e0 += NW * 32 * U) {
+          int32_t r[U];
+#pragma unroll
+          for (int t = 0; t < U; ++t) {
+            const int e = e0 + t * 32 + lane;
+            const int seg = w.find(e);
+            const int idx = w.index_in_input(e, seg);
+            r[t] = -1;
+            if (e < w.total) r[t] = __ldg(in.ri[cb + seg] + idx);
+          }
+#pragma unroll
+          for (int t = 0; t < U; ++t) {
+            const int rr = r[t] - lo;
+            if (r[t] >= 0 && rr < hi - lo) atomicOr(&bm[rr >> 5], 1u << (rr & 31));
+          }
+        }
+      }
+      __syncthreads();
+      // Popcount prefix over the slab's words (thread t owns a contiguous run).
+      const int per = (words + BLOCK - 1) / BLOCK;
+      const int w0 = threadIdx.x * per;
+      int loc = 0;
+      for (int t = 0; t < per; ++t)
+        if (w0 + t < words) loc += __popc(bm[w0 + t]);
+      int slab_u;
+      const int ex = block_excl_scan<BLOCK>(loc, red, &slab_u);
+      const int P = slab_u == 0 ? 0 : (slab_u + win_target - 1) / win_target;
+      const bool whole = (nslabs == 1 && P == 1);
+      if (P > MAX_SLAB_WINDOWS) {  // win_target is validated on the host; guard anyway
+        if (threadIdx.x == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
+      } else if (P > 0) {
+        if (threadIdx.x == 0) {
+          bnd[0] = 0;
+          cval[0] = 0;
+          bnd[P] = words;
+          cval[P] = slab_u;
+          s_wbase = atomicAdd(&ctr_w->n_windows, P);
+          s_sbase = whole ? -1 : atomicAdd(&ctr_w->n_search, P);
+        }
+        int run = ex;
+        for (int t = 0; t < per; ++t) {
+          const int wd = w0 + t;
+          if (wd >= words) break;
+          const int before = run;
+          run += __popc(bm[wd]);
+          const int pb = before / win_target, pa = run / win_target;
+          if (pa > pb && pa >= 1 && pa <= P - 1) {
+            bnd[pa] = wd + 1;
+            cval[pa] = run;
+          }
+        }
+        __syncthreads();
+        const int col_u = s_col_u;
+        for (int p = threadIdx.x; p < P; p += BLOCK) {
+          const int wi = s_wbase + p;
+          if (wi < win_cap && (whole || s_sbase + p < win_cap)) {
+            Window w;
+            w.col = j;
+            w.r_lo = whole ? 0 : lo + 32 * bnd[p];
+            w.r_hi = whole ? in.m : (int)min((int64_t)hi, (int64_t)lo + 32 * (int64_t)bnd[p + 1]);
+            w.u = cval[p + 1] - cval[p];
+            w.out_off = col_u + cval[p];
+            w.search = whole ? -1 : s_sbase + p;
+            win[wi] = w;
+            if (!whole) search_list[s_sbase + p] = wi;
+          } else {
+            atomicOr(&ctr_w->err, ERR_WINDOW_CAP);
+          }
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_col_u += slab_u;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) u_out[j] = s_col_u;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+static int blocks_per_sm(const DeviceInfo& dev, size_t smem_per_block, int threads_per_block) {
+  const size_t reserve = 1024;  // per-block system shared memory
+  int b = (int)(dev.smem_per_sm / (smem_per_block + reserve));
+  int bt = 2048 / threads_per_block;
+  if (b > bt) b = bt;
+  if (b > 32) b = 32;
+  return b < 1 ? 1 : b;
+}
+
+static int pow2_at_least(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+cudaError_t launch_sym_warp(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr,
+                            int32_t* u, uint8_t* mode, int warp_max, int sort_mode, Counters* ctr_w,
+                            const DeviceInfo& dev, cudaStream_t st) {
+  constexpr int WARPS = 8;
+  const int tmax = pow2_at_least(2 * warp_max) < 64 ? 64 : pow2_at_least(2 * warp_max);
+  const size_t smem = (size_t)WARPS * tmax * sizeof(int32_t);
+  auto kern = k_sym_warp<WARPS, 4>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = dev.sms * blocks_per_sm(dev, smem, WARPS * 32);
+  kern<<<grid, WARPS * 32, smem, st>>>(in, list, s, ctr, u, mode, tmax, sort_mode == 0 ? 1 : 0, ctr_w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sym_cta(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr, int32_t* u,
+                           Window* win, int64_t win_cap, Counters* ctr_w, int cta_max, const DeviceInfo& dev,
+                           cudaStream_t st) {
+  constexpr int BLOCK = 512;
+  const int tmax = pow2_at_least(2 * cta_max);
+  const size_t smem = (size_t)tmax * sizeof(int32_t);
+  auto kern = k_sym_cta<BLOCK, 4>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = dev.sms * blocks_per_sm(dev, smem, BLOCK);
+  kern<<<grid, BLOCK, smem, st>>>(in, list, s, ctr, u, win, win_cap, tmax, ctr_w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counters* ctr, int32_t* u, Window* win,
+                             int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
+                             const DeviceInfo& dev, cudaStream_t st) {
+  const int slab_rows = (int)(in.m < (1 << SLAB_BITS) ? in.m : (1 << SLAB_BITS));
+  const int slab_words = (slab_rows + 31) / 32 > 0 ? (slab_rows + 31) / 32 : 1;
+  const size_t smem = (size_t)slab_words * sizeof(uint32_t);
+  auto kern = k_sym_heavy<HEAVY_BLOCK, 4>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const size_t static_smem = sizeof(int) * (2 * (MAX_SLAB_WINDOWS + 1) + HEAVY_BLOCK / 32 + 4);
+  const int grid = dev.sms * blocks_per_sm(dev, smem + static_smem, HEAVY_BLOCK);
+  kern<<<grid, HEAVY_BLOCK, smem, st>>>(in, list, ctr, u, win, search_list, win_cap, window_max - 32, slab_words,
+                                        ctr_w);
+  return cudaGetLastError();
+}
+
+}  // namespace spk

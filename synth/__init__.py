@@ -32,7 +32,7 @@ import math
 
 import torch
 
-__all__ = ["er", "rmat", "spgemm_like", "random_csc", "values", "to_device", "batch_instance_params"]
+__all__ = ["er", "rmat", "spgemm_like", "random_csc", "values", "to_device", "batch_instance_params", "take_columns"]
 
 
 def _gen(seed: int, device) -> torch.Generator:
@@ -236,4 +236,24 @@ def batch_instance_params(count: int, seed: int = 0, k_range=(2, 256), mn_range=
             "L_range": L_range,
             "seed": int(seed) * 1000003 + q,
         })
+    return out
+
+
+def take_columns(A, cols: torch.Tensor):
+    """Sub-inputs holding only the listed columns, in the listed order (pure data movement)."""
+    out = []
+    for cp, ri, va in A:
+        cols_d = cols.to(cp.device)
+        cpl = cp.to(torch.int64)
+        st, en = cpl[cols_d], cpl[cols_d + 1]
+        ln = en - st
+        sub_cp = torch.zeros(cols_d.numel() + 1, dtype=torch.int64, device=cp.device)
+        sub_cp[1:] = torch.cumsum(ln, 0)
+        tot = int(sub_cp[-1])
+        if tot:
+            seg = torch.repeat_interleave(torch.arange(cols_d.numel(), device=cp.device), ln)
+            idx = st[seg] + torch.arange(tot, device=cp.device) - sub_cp[:-1][seg]
+        else:
+            idx = torch.zeros(0, dtype=torch.int64, device=cp.device)
+        out.append((sub_cp.to(torch.int32), ri[idx], va[idx]))
     return out

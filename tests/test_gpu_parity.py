@@ -1,0 +1,281 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar: col_ptr and row_idx bit-exact; values bit-exact for small-integer fp64
+inputs, otherwise per entry |gpu - oracle| <= 1e-12 * sum|terms| (fp64) or
+1e-5 * sum|terms| (fp32).  Small cases compare every entry; the full-size
+workloads compare sampled columns (the heaviest ones and a random set) with
+the oracle and check size-independent invariants on every column.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2112_10223_gb300 as spk
+import synth
+from spk_testlib import (check_full, check_global_invariants, check_sampled, compare, run_gpu, sample_columns,
+                         to_np)
+
+pytestmark = pytest.mark.gpu
+
+F64, F32 = torch.float64, torch.float32
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    spk.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def test_er_k4_1024_small_integers_bit_exact():
+    """k = 4 ER 1024 x 1024, 8 distinct rows per column, fp64 integers in [-8, 8] \\ {0}, seed 0."""
+    A = synth.er(4, 1024, 1024, 8, seed=0, dtype=F64, value_kind="int8")
+    info, _ = check_full(A, 1024, F64, exact=True)
+    assert info["cols_warp"] == 1024
+    assert info["cols_ordered"] == 1024
+
+
+@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("dtype", [F64, F32])
+@pytest.mark.parametrize("seed", range(3))
+def test_irregular_small(seed, dtype, sort_mode):
+    A = synth.random_csc(7, 300, 257, density=0.05, seed=seed, dtype=dtype, empty_matrix_frac=0.1)
+    check_full(A, 300, dtype, options=spk.default_options(sort_mode=sort_mode))
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_classes_forced_small_thresholds(dtype):
+    """Tiny thresholds push ordinary columns through the CTA and heavy-bitmap paths."""
+    A = synth.random_csc(9, 500, 200, density=0.08, seed=4, dtype=dtype)
+    opt = spk.default_options(warp_max=4, cta_max=16)
+    info, _ = check_full(A, 500, dtype, options=opt)
+    assert info["cols_cta"] > 0 and info["cols_heavy"] > 0
+
+
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_rmat_split_windows(dtype):
+    """R-MAT scale 14: heavy columns with more distinct rows than one window holds."""
+    A = synth.rmat(32, 14, 16, seed=1, dtype=dtype)
+    opt = spk.default_options(warp_max=32, cta_max=64, window_max=1024)
+    info, _ = check_full(A, 1 << 14, dtype, options=opt)
+    assert info["windows_split"] > 0, info
+
+
+def test_rmat_default_thresholds():
+    A = synth.rmat(16, 13, 16, seed=2, dtype=F32)
+    info, _ = check_full(A, 1 << 13, F32)
+    assert info["cols_heavy"] > 0
+
+
+def test_heavy_columns_span_two_row_slabs():
+    """m > 2^20: the heavy symbolic pass runs its bitmap over two row slabs."""
+    m = (1 << 20) + 4099
+    A = synth.er(6, m, 5, 1500, seed=3, dtype=F64, value_kind="int8")
+    info, _ = check_full(A, m, F64, exact=True, options=spk.default_options(window_max=1024))
+    assert info["cols_heavy"] == 5 and info["windows_split"] > 0
+
+
+def test_spgemm_like_overlapping_patterns():
+    A = synth.spgemm_like(40, 2000, 300, 24, seed=5, dtype=F64)
+    info, _ = check_full(A, 2000, F64)
+    assert info["nnz_out"] <= 300 * 96
+
+
+def test_k1_identity():
+    A = synth.random_csc(1, 200, 150, density=0.1, seed=6, dtype=F64)
+    cp, ri, va = run_gpu(A, 200)
+    assert np.array_equal(cp.cpu().numpy(), A[0][0].numpy().astype(np.int64))
+    assert np.array_equal(ri.cpu().numpy(), A[0][1].numpy())
+    assert np.array_equal(va.cpu().numpy(), A[0][2].numpy())
+
+
+def test_all_empty_and_zero_columns():
+    A = [(torch.zeros(51, dtype=torch.int32), torch.zeros(0, dtype=torch.int32), torch.zeros(0, dtype=F64))
+         for _ in range(3)]
+    cp, ri, va = run_gpu(A, 10)
+    assert cp.cpu().tolist() == [0] * 51 and ri.numel() == 0 and va.numel() == 0
+
+
+def test_single_row_matrices():
+    A = synth.random_csc(5, 1, 400, density=0.5, seed=7, dtype=F64, value_kind="int8")
+    check_full(A, 1, F64, exact=True)
+
+
+def test_full_dense_column_and_last_row():
+    m, k = 3000, 6
+    rows = torch.arange(m, dtype=torch.int32)
+    A = []
+    for i in range(k):
+        cp = torch.tensor([0, 0, m, m + 1], dtype=torch.int32)  # col 0 empty, col 1 full, col 2 = last row
+        ri = torch.cat([rows, torch.tensor([m - 1], dtype=torch.int32)])
+        A.append((cp, ri, synth.values(torch.Generator().manual_seed(i), m + 1, F64, "int8", "cpu")))
+    check_full(A, m, F64, exact=True)
+
+
+def test_identical_inputs_compression_k():
+    A1 = synth.er(1, 5000, 400, 40, seed=8, dtype=F64, value_kind="int8")
+    A = A1 * 24  # cf = 24
+    info, _ = check_full(A, 5000, F64, exact=True)
+    assert info["nnz_out"] == 400 * 40
+
+
+@pytest.mark.parametrize("s", [511, 512, 513, 4095, 4096, 4097])
+def test_class_boundaries(s):
+    """Columns whose summed input count sits on each side of the class limits."""
+    k = 8
+    m = 20000
+    per = [s // k + (1 if i < s % k else 0) for i in range(k)]
+    g = torch.Generator().manual_seed(s)
+    A = []
+    for i in range(k):
+        rows = torch.randperm(m, generator=g)[:per[i]].sort().values.to(torch.int32)
+        A.append((torch.tensor([0, per[i]], dtype=torch.int32), rows, synth.values(g, per[i], F64, "int8", "cpu")))
+    check_full(A, m, F64, exact=True)
+
+
+def test_cancellation_keeps_positive_zero():
+    A = synth.random_csc(1, 400, 300, density=0.05, seed=9, dtype=F64)
+    A = A + [(A[0][0], A[0][1], -A[0][2])]
+    cp, ri, va = run_gpu(A, 400)
+    v = va.cpu().numpy()
+    assert len(v) == A[0][1].numel() and (v == 0).all() and not np.signbit(v).any()
+
+
+def test_many_inputs_span_several_chunks():
+    A = synth.random_csc(300, 900, 60, density=0.01, seed=10, dtype=F32)
+    check_full(A, 900, F32)
+
+
+def test_permutation_invariance_indices_bit_identical():
+    A = synth.random_csc(12, 700, 300, density=0.03, seed=11, dtype=F64)
+    B1 = run_gpu(A, 700)
+    perm = torch.randperm(12, generator=torch.Generator().manual_seed(0)).tolist()
+    B2 = run_gpu([A[p] for p in perm], 700)
+    assert torch.equal(B1[0], B2[0]) and torch.equal(B1[1], B2[1])
+    np.testing.assert_allclose(B1[2].cpu().numpy(), B2[2].cpu().numpy(), rtol=0, atol=1e-13)
+
+
+def test_repeated_runs_indices_bit_identical():
+    A = synth.rmat(8, 12, 8, seed=12, dtype=F32)
+    outs = [run_gpu(A, 1 << 12) for _ in range(3)]
+    for o in outs[1:]:
+        assert torch.equal(o[0], outs[0][0]) and torch.equal(o[1], outs[0][1])
+
+
+# ---------------------------------------------------------------- error paths
+def _plan(A, m, **opts):
+    Ad = [tuple(t.cuda() for t in a) for a in A]
+    return spk.spkadd_plan(Ad, m, options=spk.default_options(**opts))
+
+
+def test_validate_accepts_valid_input():
+    A = synth.random_csc(3, 50, 40, density=0.2, seed=13, dtype=F64)
+    h = _plan(A, 50, validate=1)
+    spk.spkadd_destroy(h)
+
+
+def test_validate_rejects_unsorted_rows():
+    cp = torch.tensor([0, 3], dtype=torch.int32)
+    A = [(cp, torch.tensor([1, 5, 3], dtype=torch.int32), torch.ones(3, dtype=F64))]
+    with pytest.raises(spk.SpkaddError) as e:
+        _plan(A, 10, validate=1)
+    assert e.value.status == 3
+
+
+def test_validate_rejects_duplicate_rows():
+    cp = torch.tensor([0, 2], dtype=torch.int32)
+    A = [(cp, torch.tensor([4, 4], dtype=torch.int32), torch.ones(2, dtype=F64))]
+    with pytest.raises(spk.SpkaddError) as e:
+        _plan(A, 10, validate=1)
+    assert e.value.status == 3
+
+
+def test_validate_rejects_row_out_of_range():
+    cp = torch.tensor([0, 2], dtype=torch.int32)
+    A = [(cp, torch.tensor([4, 10], dtype=torch.int32), torch.ones(2, dtype=F64))]
+    with pytest.raises(spk.SpkaddError) as e:
+        _plan(A, 10, validate=1)
+    assert e.value.status == 4
+
+
+def test_validate_rejects_bad_col_ptr():
+    cp = torch.tensor([0, 3, 2], dtype=torch.int32)
+    A = [(cp, torch.tensor([1, 2], dtype=torch.int32), torch.ones(2, dtype=F64))]
+    with pytest.raises(spk.SpkaddError) as e:
+        _plan(A, 10, validate=1)
+    assert e.value.status == 4
+
+
+def test_numeric_before_symbolic_is_a_state_error():
+    A = synth.random_csc(2, 30, 20, density=0.2, seed=14, dtype=F64)
+    h = _plan(A, 30)
+    cp = torch.empty(21, dtype=torch.int64, device="cuda")
+    with pytest.raises(spk.SpkaddError) as e:
+        spk.spkadd_numeric(h, cp, torch.empty(100, dtype=torch.int32, device="cuda"),
+                           torch.empty(100, dtype=F64, device="cuda"))
+    assert e.value.status == 9
+    spk.spkadd_destroy(h)
+
+
+def test_user_allocator_and_allocation_failure():
+    A = synth.random_csc(4, 100, 80, density=0.1, seed=15, dtype=F64)
+    Ad = [tuple(t.cuda() for t in a) for a in A]
+    live = {}
+
+    @spk.ALLOC_FN
+    def alloc(nbytes, stream, ctx):
+        t = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    @spk.FREE_FN
+    def free(ptr, stream, ctx):
+        live.pop(ptr, None)
+
+    o = spk.default_options()
+    o.alloc, o.free = alloc, free
+    cp, ri, va = spk.spkadd(Ad, 100, options=o)
+    torch.cuda.synchronize()
+    want = oracle.add(to_np(A))
+    compare((cp.cpu().numpy(), ri.cpu().numpy(), va.cpu().numpy()), want, F64)
+
+    @spk.ALLOC_FN
+    def failing(nbytes, stream, ctx):
+        return None
+
+    o2 = spk.default_options()
+    o2.alloc, o2.free = failing, free
+    with pytest.raises(spk.SpkaddError) as e:
+        spk.spkadd_plan(Ad, 100, options=o2)
+    assert e.value.status == 6
+
+
+# ---------------------------------------------------------- full-size workloads
+def test_er_k32_2pow20_d16_fp64_sampled():
+    """k = 32 ER 2^20 x 2^20, 16 distinct rows per column, fp64 uniform [-1, 1]; sampled columns vs oracle."""
+    dev = torch.device("cuda:0")
+    A = synth.er(32, 1 << 20, 1 << 20, 16, seed=0, dtype=F64, device=dev)
+    B, info = None, None
+    cp, ri, va, info = spk.spkadd(A, 1 << 20, info=True)
+    torch.cuda.synchronize()
+    B = (cp, ri, va)
+    assert info["cols_warp"] == 1 << 20
+    check_global_invariants(A, B, 1 << 20)
+    cols, _ = sample_columns(A, 3000, 16, seed=1)
+    check_sampled(A, B, 1 << 20, cols, F64)
+
+
+def test_rmat_k64_scale20_fp32_sampled():
+    """k = 64 independent R-MAT scale 20, edge factor 16, (.57, .19, .19, .05), fp32; sampled columns vs oracle."""
+    dev = torch.device("cuda:0")
+    A = synth.rmat(64, 20, 16, seed=0, dtype=F32, device=dev)
+    cp, ri, va, info = spk.spkadd(A, 1 << 20, info=True)
+    torch.cuda.synchronize()
+    B = (cp, ri, va)
+    assert info["cols_heavy"] > 0 and info["windows_split"] > 0
+    check_global_invariants(A, B, 1 << 20)
+    cols, _ = sample_columns(A, 3000, 48, seed=2)
+    check_sampled(A, B, 1 << 20, cols, F32)
