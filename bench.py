@@ -48,6 +48,8 @@ WORKLOADS = {
     "er_k32_m2p20_d16_f64": dict(family="er", k=32, m=1 << 20, n=1 << 20, d=16, dtype=torch.float64),
     "rmat_k64_s20_ef16_f32": dict(family="rmat", k=64, scale=20, ef=16, dtype=torch.float32),
     "er_k4_m1024_d8_f64int": dict(family="er", k=4, m=1024, n=1024, d=8, dtype=torch.float64, value_kind="int8"),
+    # profiling case: the default workload with a quarter of the columns (1.6 GB of input, still > L2)
+    "er_k32_m2p20_n2p18_d16_f64": dict(family="er", k=32, m=1 << 20, n=1 << 18, d=16, dtype=torch.float64),
 }
 DEFAULT_WORKLOAD = "er_k32_m2p20_d16_f64"
 
@@ -379,7 +381,7 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
         "classes": {x: info[x] for x in ("cols_warp", "cols_cta", "cols_heavy", "windows", "windows_split",
-                                         "cols_ordered")},
+                                         "cols_unique")},
     }
     print(json.dumps(out))
 

@@ -109,9 +109,9 @@ typedef struct spkadd_options {
     /* Maximum distinct rows per numeric row window of a heavy column
      * (range 1024..4096). */
     int32_t window_max;
-    /* 0 = adaptive (order-preserving hash for columns whose rows spread
-     * evenly, scrambled hash + counting sort otherwise); 1 = always the
-     * scrambled hash + counting sort. */
+    /* 0 = default.  1 = warp-class columns always take the duplicate-merging
+     * path of the numeric pass, even when the symbolic pass found no repeated
+     * row (a test and diagnosis switch; results are the same). */
     int32_t sort_mode;
     /* Workspace allocator.  NULL alloc: cudaMallocAsync / cudaFreeAsync on
      * the plan's stream.  Otherwise alloc(bytes, stream, ctx) must return
@@ -132,7 +132,7 @@ typedef struct spkadd_info {
     int64_t cols_heavy;
     int64_t windows;        /* numeric thread-block work items (CTA columns + heavy windows) */
     int64_t windows_split;  /* of those, row windows that needed per-input binary searches */
-    int64_t cols_ordered;   /* warp columns summed with the order-preserving hash */
+    int64_t cols_unique;    /* warp columns in which no row repeats across the inputs */
     int64_t workspace_bytes;
     int64_t kernel_launches; /* kernels this handle has launched so far */
 } spkadd_info;

@@ -65,7 +65,7 @@ class Options(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "k", "m", "n", "nnz_in", "nnz_out", "cols_warp", "cols_cta", "cols_heavy", "windows", "windows_split",
-        "cols_ordered", "workspace_bytes", "kernel_launches")]
+        "cols_unique", "workspace_bytes", "kernel_launches")]
 
 
 _lib = None

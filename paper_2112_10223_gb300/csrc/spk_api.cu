@@ -108,7 +108,6 @@ struct spkadd_handle {
   Inputs in{};
   const int64_t* d_nnz = nullptr;
   int32_t *d_s = nullptr, *d_u = nullptr;
-  uint8_t* d_mode = nullptr;
   int32_t *d_wl = nullptr, *d_cl = nullptr, *d_hl = nullptr;
   Window* d_win = nullptr;
   int32_t* d_search = nullptr;
@@ -236,7 +235,6 @@ SPK_API spkadd_status spkadd_plan(spkadd_handle** hp, int k, const spkadd_csc* A
   const size_t o_ctr = cv.take<Counters>(1);
   const size_t o_s = cv.take<int32_t>(n);
   const size_t o_u = cv.take<int32_t>(n);
-  const size_t o_mode = cv.take<uint8_t>(n);
   const size_t o_wl = cv.take<int32_t>(n);
   const size_t o_cl = cv.take<int32_t>(n);
   const size_t o_hl = cv.take<int32_t>(n);
@@ -254,7 +252,6 @@ SPK_API spkadd_status spkadd_plan(spkadd_handle** hp, int k, const spkadd_csc* A
   h->d_ctr = reinterpret_cast<Counters*>(h->ws + o_ctr);
   h->d_s = reinterpret_cast<int32_t*>(h->ws + o_s);
   h->d_u = reinterpret_cast<int32_t*>(h->ws + o_u);
-  h->d_mode = reinterpret_cast<uint8_t*>(h->ws + o_mode);
   h->d_wl = reinterpret_cast<int32_t*>(h->ws + o_wl);
   h->d_cl = reinterpret_cast<int32_t*>(h->ws + o_cl);
   h->d_hl = reinterpret_cast<int32_t*>(h->ws + o_hl);
@@ -329,8 +326,8 @@ SPK_API spkadd_status spkadd_symbolic(spkadd_handle* h, int64_t* nnz_B) {
       ce = spk::launch_sym_cta(h->in, h->d_cl, h->d_s, h->d_ctr, h->d_u, h->d_win, h->win_cap, h->d_ctr,
                                h->opt.cta_max, h->dev, h->st);
     if (ce == cudaSuccess)
-      ce = spk::launch_sym_warp(h->in, h->d_wl, h->d_s, h->d_ctr, h->d_u, h->d_mode, h->opt.warp_max,
-                                h->opt.sort_mode, h->d_ctr, h->dev, h->st);
+      ce = spk::launch_sym_warp(h->in, h->d_wl, h->d_s, h->d_ctr, h->d_u, h->opt.warp_max, h->d_ctr, h->dev,
+                                h->st);
     h->launches += 3;
   }
   if (ce == cudaSuccess) ce = spk::launch_scan(h->d_u, (int)h->n, h->d_scan, h->d_colptr, h->st);
@@ -381,8 +378,8 @@ SPK_API spkadd_status spkadd_numeric(spkadd_handle* h, int64_t* B_col_ptr, int32
                              h->dev, h->st);
   h->launches += cta_items > 0;
   if (ce == cudaSuccess && h->h_ctr.n_warp > 0)
-    ce = spk::launch_num_warp(h->in, f64, h->d_wl, h->h_ctr.n_warp, h->d_u, h->d_mode, h->d_colptr, B_row_idx, B_val,
-                              h->opt.warp_max, h->d_ctr, h->dev, h->st);
+    ce = spk::launch_num_warp(h->in, f64, h->d_wl, h->h_ctr.n_warp, h->d_s, h->d_u, h->d_colptr, B_row_idx, B_val,
+                              h->opt.warp_max, h->opt.sort_mode, h->d_ctr, h->dev, h->st);
   h->launches += h->h_ctr.n_warp > 0;
   if (ce != cudaSuccess) return from_cuda(ce);
   h->state = ST_NUMERIC;
@@ -408,7 +405,7 @@ SPK_API spkadd_status spkadd_get_info(spkadd_handle* h, spkadd_info* info) {
   info->cols_heavy = c.n_heavy;
   info->windows = c.n_windows;
   info->windows_split = c.n_search;
-  info->cols_ordered = c.n_ordered;
+  info->cols_unique = c.n_unique;
   info->workspace_bytes = (int64_t)(h->ws_bytes + h->offs_bytes);
   info->kernel_launches = h->launches;
   return from_device_err(c.err);

@@ -36,7 +36,7 @@ struct Counters {
   int32_t n_warp, n_cta, n_heavy;
   int32_t n_windows;    // Window records appended
   int32_t n_search;     // of those, split windows needing per-input offsets
-  int32_t n_ordered;    // warp columns the symbolic pass found evenly spread
+  int32_t n_unique;     // warp columns whose input rows are all distinct (u_j == s_j)
   int32_t err;
   int32_t pad;
 };
@@ -135,6 +135,50 @@ struct SegWalk {
   }
   __device__ __forceinline__ int index_in_input(int e, int seg) const {
     return e + __shfl_sync(SPK_FULL, delta, seg);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Chunk map: the segment walker plus a fast path for chunks whose segments all
+// have one length L (Erdos-Renyi and partial-product inputs give every input
+// the same count per column).  Then position e lies in segment e / L, found
+// with one multiply-high instead of five shuffles.  `nvalid` is the number of
+// real inputs in the chunk (lanes at or beyond it carry empty segments).
+// ---------------------------------------------------------------------------
+struct ChunkMap {
+  SegWalk w;
+  int beg;          // this lane's segment begin (fast path)
+  int total;
+  int L;
+  uint64_t magic;   // ceil(2^32 / L): e / L == (e * magic) >> 32 for e < 2^16, L <= 2^16
+  bool equal;
+
+  __device__ __forceinline__ void init(int beg_, int len, int lane, int nvalid) {
+    beg = beg_;
+    const int L0 = __shfl_sync(SPK_FULL, len, 0);
+    equal = __all_sync(SPK_FULL, lane >= nvalid || len == L0) && L0 > 0 && L0 <= 65536 &&
+            (int64_t)L0 * nvalid < 65536;
+    if (equal) {
+      L = L0;
+      total = L0 * nvalid;
+      magic = (0xFFFFFFFFull / (uint64_t)L0) + 1ull;
+    } else {
+      w.init(beg_, len, lane);
+      total = w.total;
+    }
+  }
+  // Element index (inside its input) of flattened position e; *seg = segment.
+  // Every lane must call it (it shuffles).
+  __device__ __forceinline__ int locate(int e, int* seg) const {
+    if (equal) {
+      const int sg = (int)(((uint64_t)(uint32_t)e * magic) >> 32);
+      const int b = __shfl_sync(SPK_FULL, beg, sg & 31);
+      *seg = sg;
+      return b + (e - sg * L);
+    }
+    const int sg = w.find(e);
+    *seg = sg;
+    return w.index_in_input(e, sg);
   }
 };
 

@@ -32,8 +32,7 @@ cudaError_t launch_window_search(const Inputs& in, const Window* win, const int3
                                  int32_t* offs, int sms, cudaStream_t st);
 
 cudaError_t launch_sym_warp(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr,
-                            int32_t* u, uint8_t* mode, int warp_max, int sort_mode, Counters* ctr_w,
-                            const DeviceInfo& dev, cudaStream_t st);
+                            int32_t* u, int warp_max, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
 cudaError_t launch_sym_cta(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr, int32_t* u,
                            Window* win, int64_t win_cap, Counters* ctr_w, int cta_max, const DeviceInfo& dev,
                            cudaStream_t st);
@@ -41,9 +40,9 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counte
                              int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
                              const DeviceInfo& dev, cudaStream_t st);
 
-cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, int n_cols, const int32_t* u,
-                            const uint8_t* mode, const int64_t* col_ptr, int32_t* out_row, void* out_val,
-                            int warp_max, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
+cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, int n_cols, const int32_t* s,
+                            const int32_t* u, const int64_t* col_ptr, int32_t* out_row, void* out_val,
+                            int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
 cudaError_t launch_num_cta(const Inputs& in, bool f64, const Window* win, int n_win, const int32_t* offs,
                            const int64_t* col_ptr, int32_t* out_row, void* out_val, int window_max,
                            Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);

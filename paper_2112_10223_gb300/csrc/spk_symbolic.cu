@@ -2,10 +2,8 @@
 //
 // Warp class (s_j <= warp_max): one warp per column, a shared-memory
 //   open-addressing table of keys only (Alg. 6 HashSymbolic), size a power of
-//   two >= 2 s_j, linear probing, atomicCAS on the row key.  The table first
-//   tries an order-preserving home slot floor(r * T / m); a column whose
-//   longest probe stays short is marked "ordered" for the numeric pass, which
-//   then gets the sorted output from the table layout instead of a sort.
+//   two >= 4 s_j, scrambled multiplicative hash, linear probing, atomicCAS on
+//   the row key.
 // CTA class (s_j <= cta_max): one thread block per column, same table with the
 //   scrambled (multiplicative) hash.  Emits one numeric work item per column.
 // Heavy class: one thread block per column with a shared-memory bitmap of a
@@ -19,23 +17,22 @@
 
 namespace spk {
 
-constexpr int PROBE_CAP = 32;  // longest probe an "ordered" warp column may need
-
 template <int WARPS, int U>
 __global__ void __launch_bounds__(WARPS * 32) k_sym_warp(Inputs in, const int32_t* __restrict__ list,
                                                          const int32_t* __restrict__ s_arr,
                                                          const Counters* __restrict__ ctr,
-                                                         int32_t* __restrict__ u_out, uint8_t* __restrict__ mode_out,
-                                                         int tmax, int try_ordered, Counters* ctr_w) {
+                                                         int32_t* __restrict__ u_out, int tmax, Counters* ctr_w) {
   extern __shared__ int32_t sm_keys[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int32_t* keys = sm_keys + wid * tmax;
   const int ncols = ctr->n_warp;
-  int n_ord = 0;
+  int n_unique = 0;
   for (int c = blockIdx.x * WARPS + wid; c < ncols; c += gridDim.x * WARPS) {
     const int j = list[c];
     const int s = s_arr[j];
-    const int q = max(6, ceil_log2(2 * s));
+    // Table of 2^q >= 4 s_j slots: load factor <= 1/4 keeps the probe loops of
+    // the 32 lanes short and alike.
+    const int q = max(6, ceil_log2(4 * s));
     const int T = 1 << q;
     if (T > tmax) {  // cannot happen for a warp-class column; guard the shared table
       if (lane == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
@@ -43,7 +40,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_sym_warp(Inputs in, const int32_
     }
     for (int p = lane; p < T; p += 32) keys[p] = -1;
     __syncwarp();
-    int newc = 0, maxp = 0;
+    int newc = 0;
     for (int cb = 0; cb < in.k; cb += 32) {
       const int i = cb + lane;
       int beg = 0, len = 0;
@@ -52,24 +49,23 @@ __global__ void __launch_bounds__(WARPS * 32) k_sym_warp(Inputs in, const int32_
         beg = __ldg(cp + j);
         len = __ldg(cp + j + 1) - beg;
       }
-      SegWalk w;
-      w.init(beg, len, lane);
-      for (int e0 = 0; e0 < w.total; e0 += 32 * U) {
+      ChunkMap cm;
+      cm.init(beg, len, lane, min(32, in.k - cb));
+      for (int e0 = 0; e0 < cm.total; e0 += 32 * U) {
         int32_t r[U];
 #pragma unroll
         for (int t = 0; t < U; ++t) {
           const int e = e0 + t * 32 + lane;
-          const int seg = w.find(e);
-          const int idx = w.index_in_input(e, seg);
+          int seg;
+          const int idx = cm.locate(e, &seg);
           r[t] = -1;
-          if (e < w.total) r[t] = __ldg(in.ri[cb + seg] + idx);
+          if (e < cm.total) r[t] = __ldg(in.ri[cb + seg] + idx);
         }
 #pragma unroll
         for (int t = 0; t < U; ++t) {
           if (r[t] < 0) continue;
-          uint32_t h = (try_ordered ? hash_ordered(r[t], in.home_mul, q) : hash_scrambled(r[t], q)) & (T - 1);
-          int probes = 0;
-          for (; probes < T; ++probes) {  // T > s_j keys: an empty slot is always found
+          uint32_t h = hash_scrambled(r[t], q);
+          for (int probes = 0; probes < T; ++probes) {  // T > s_j keys: an empty slot is always found
             const int old = atomicCAS(&keys[h], -1, r[t]);
             if (old == -1) {
               ++newc;
@@ -78,21 +74,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_sym_warp(Inputs in, const int32_
             if (old == r[t]) break;
             h = (h + 1) & (T - 1);
           }
-          maxp = max(maxp, probes);
         }
       }
     }
     newc = warp_sum(newc);
-    maxp = warp_max(maxp);
     if (lane == 0) {
       u_out[j] = newc;
-      const int ord = (try_ordered && maxp <= PROBE_CAP) ? 1 : 0;
-      mode_out[j] = (uint8_t)ord;
-      n_ord += ord;
+      n_unique += (newc == s);
     }
     __syncwarp();
   }
-  if (lane == 0 && n_ord) atomicAdd(&ctr_w->n_ordered, n_ord);
+  if (lane == 0 && n_unique) atomicAdd(&ctr_w->n_unique, n_unique);
 }
 
 template <int BLOCK, int U>
@@ -317,16 +309,15 @@ static int pow2_at_least(int x) {
 }
 
 cudaError_t launch_sym_warp(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr,
-                            int32_t* u, uint8_t* mode, int warp_max, int sort_mode, Counters* ctr_w,
-                            const DeviceInfo& dev, cudaStream_t st) {
+                            int32_t* u, int warp_max, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
   constexpr int WARPS = 8;
-  const int tmax = pow2_at_least(2 * warp_max) < 64 ? 64 : pow2_at_least(2 * warp_max);
+  const int tmax = pow2_at_least(4 * warp_max) < 64 ? 64 : pow2_at_least(4 * warp_max);
   const size_t smem = (size_t)WARPS * tmax * sizeof(int32_t);
-  auto kern = k_sym_warp<WARPS, 4>;
+  auto kern = k_sym_warp<WARPS, 8>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = dev.sms * blocks_per_sm(dev, smem, WARPS * 32);
-  kern<<<grid, WARPS * 32, smem, st>>>(in, list, s, ctr, u, mode, tmax, sort_mode == 0 ? 1 : 0, ctr_w);
+  kern<<<grid, WARPS * 32, smem, st>>>(in, list, s, ctr, u, tmax, ctr_w);
   return cudaGetLastError();
 }
 

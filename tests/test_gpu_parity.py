@@ -35,7 +35,9 @@ def test_er_k4_1024_small_integers_bit_exact():
     A = synth.er(4, 1024, 1024, 8, seed=0, dtype=F64, value_kind="int8")
     info, _ = check_full(A, 1024, F64, exact=True)
     assert info["cols_warp"] == 1024
-    assert info["cols_ordered"] == 1024
+    u = oracle.union_sizes(to_np(A))
+    s = sum((a[0][1:] - a[0][:-1]).numpy() for a in A)
+    assert info["cols_unique"] == int((u == s).sum())
 
 
 @pytest.mark.parametrize("sort_mode", [0, 1])
@@ -50,9 +52,9 @@ def test_irregular_small(seed, dtype, sort_mode):
 def test_classes_forced_small_thresholds(dtype):
     """Tiny thresholds push ordinary columns through the CTA and heavy-bitmap paths."""
     A = synth.random_csc(9, 500, 200, density=0.08, seed=4, dtype=dtype)
-    opt = spk.default_options(warp_max=4, cta_max=16)
+    opt = spk.default_options(warp_max=250, cta_max=320)
     info, _ = check_full(A, 500, dtype, options=opt)
-    assert info["cols_cta"] > 0 and info["cols_heavy"] > 0
+    assert info["cols_warp"] > 0 and info["cols_cta"] > 0 and info["cols_heavy"] > 0, info
 
 
 @pytest.mark.parametrize("dtype", [F32, F64])
