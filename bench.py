@@ -47,6 +47,8 @@ WORKLOADS = {
     # name: (family, k, m, n, d or scale, dtype)
     "er_k32_m2p20_d16_f64": dict(family="er", k=32, m=1 << 20, n=1 << 20, d=16, dtype=torch.float64),
     "rmat_k64_s20_ef16_f32": dict(family="rmat", k=64, scale=20, ef=16, dtype=torch.float32),
+    # profiling case: the R-MAT workload at scale 18 (2.6e8 input nnz, 2 GB, still > L2)
+    "rmat_k64_s18_ef16_f32": dict(family="rmat", k=64, scale=18, ef=16, dtype=torch.float32),
     "er_k4_m1024_d8_f64int": dict(family="er", k=4, m=1024, n=1024, d=8, dtype=torch.float64, value_kind="int8"),
     # profiling case: the default workload with a quarter of the columns (1.6 GB of input, still > L2)
     "er_k32_m2p20_n2p18_d16_f64": dict(family="er", k=32, m=1 << 20, n=1 << 18, d=16, dtype=torch.float64),

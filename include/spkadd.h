@@ -183,6 +183,34 @@ spkadd_status spkadd_get_info(spkadd_handle* h, spkadd_info* info);
 /* Frees the workspace (stream-ordered) and the handle.  NULL is accepted. */
 spkadd_status spkadd_destroy(spkadd_handle* h);
 
+/*
+ * Exclusive scan of per-column counts into CSC column pointers, allocating
+ * nothing: col_ptr[0] = 0 and col_ptr[j+1] = col_ptr[j] + counts[j] -- the
+ * scan spkadd_symbolic runs on nnz(B(:,j)).  The paper has no counterpart of
+ * this entry point.  It exists for callers that must not allocate device
+ * memory inside a call: services that hand all of a GPU's memory to their own
+ * arena up front (so a cudaMalloc would fail or break their accounting), and
+ * latency-critical code for which cudaMalloc's implicit device-wide
+ * synchronisation is not acceptable.
+ *   counts   device, n int32 counts, each >= 0
+ *   n        0 <= n <= SPKADD_SCAN_NOALLOC_MAX_N; a larger n returns
+ *            SPKADD_ERR_UNSUPPORTED and launches nothing
+ *   col_ptr  device, n+1 int64, caller-allocated (written)
+ *   stream   cudaStream_t (as void*); enqueued, does not block
+ * Scratch: one fixed array of SPKADD_SCAN_NOALLOC_MAX_N / 4096 + 1 int64
+ * (32 KB) defined inside the library; every GPU that loads the library holds
+ * it until the process exits.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents; nothing needs to start at zero
+ * (every element a call reads, that call wrote first).  Calls that can
+ * overlap on the GPU -- on different streams without ordering between them,
+ * or from several host threads -- race on the array and give wrong results.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define SPKADD_SCAN_NOALLOC_MAX_N (4096 * 4096)
+spkadd_status spkadd_scan_counts_noalloc(const int32_t* counts, int64_t n, int64_t* col_ptr, void* stream);
+
 /* Static, human-readable name of a status code. */
 const char* spkadd_status_string(spkadd_status s);
 

@@ -30,8 +30,10 @@ from ._build import LIB_PATH, build  # noqa: F401  (build is re-exported)
 __all__ = [
     "SpkaddError", "Options", "Info", "library", "default_options", "spkadd_plan", "spkadd_symbolic",
     "spkadd_numeric", "spkadd_destroy", "spkadd_get_info", "spkadd_status_string", "spkadd", "Handle",
-    "STATUS",
+    "STATUS", "spkadd_scan_counts_noalloc", "SCAN_NOALLOC_MAX_N",
 ]
+
+SCAN_NOALLOC_MAX_N = 4096 * 4096
 
 STATUS = {
     0: "SPKADD_OK", 1: "SPKADD_ERR_INVALID_ARG", 2: "SPKADD_ERR_SHAPE_MISMATCH", 3: "SPKADD_ERR_UNSORTED",
@@ -96,6 +98,8 @@ def library():
         lib.spkadd_status_string.restype = ctypes.c_char_p
         lib.spkadd_version.argtypes = []
         lib.spkadd_version.restype = ctypes.c_int
+        lib.spkadd_scan_counts_noalloc.argtypes = [P, ctypes.c_int64, P, P]
+        lib.spkadd_scan_counts_noalloc.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -223,3 +227,21 @@ def spkadd(A, m: int, dtype=None, stream=None, options: Options | None = None, i
     finally:
         spkadd_destroy(h)
     return (col_ptr, row_idx, val, stats) if info else (col_ptr, row_idx, val)
+
+
+def spkadd_scan_counts_noalloc(counts: torch.Tensor, col_ptr: torch.Tensor, stream=None) -> None:
+    """col_ptr = exclusive scan of counts (int32 -> int64) without any device allocation.
+
+    For callers that must not allocate device memory inside a call (memory
+    handed to their own arena up front, or no room for cudaMalloc's implicit
+    synchronisation).  The library keeps a fixed 32 KB scratch array per GPU;
+    calls that can overlap on the GPU race on it.  The first call on a device
+    should come before any stream capture.
+    """
+    if counts.dtype != torch.int32 or not counts.is_cuda or not counts.is_contiguous():
+        raise TypeError("counts must be a contiguous int32 CUDA tensor")
+    if col_ptr.dtype != torch.int64 or not col_ptr.is_cuda or col_ptr.numel() != counts.numel() + 1:
+        raise TypeError("col_ptr must be an int64 CUDA tensor with len(counts) + 1 elements")
+    _, sp = _stream_ptr(stream)
+    _check(library().spkadd_scan_counts_noalloc(counts.data_ptr() if counts.numel() else None, counts.numel(),
+                                                col_ptr.data_ptr(), sp), "spkadd_scan_counts_noalloc")
