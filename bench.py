@@ -87,7 +87,7 @@ def read_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("spk_numeric.cu", "spk_common.cuh"):
+    for f in ("spk_warp.cu", "spk_common.cuh"):
         with open(os.path.join(ROOT, "paper_2112_10223_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -374,7 +374,7 @@ def run_ours(args, world, rank, local):
                    "cf": nnz_in / max(nnz_out, 1), "l2": "inputs exceed the 129 MB L2; no flush between steps",
                    "parallelism": f"{world} independent instance(s), one per GPU", "seed": args.seed},
         "hbm_gbs_step": step_gbs,
-        "roofline": {"kernel": "k_num_warp (spkadd_numeric)", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": "k_warp_col<numeric> (spkadd_numeric)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": read_traffic(args.workload), "algorithmic_bytes": alg,
                      "launch_ms": num_avg, "step_frac": step_gbs / peak},

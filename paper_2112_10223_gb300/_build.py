@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libspkadd.so")
-SOURCES = ["spk_api.cu", "spk_plan.cu", "spk_symbolic.cu", "spk_numeric.cu", "spk_noalloc.cu"]
+SOURCES = ["spk_api.cu", "spk_plan.cu", "spk_symbolic.cu", "spk_numeric.cu", "spk_noalloc.cu", "spk_warp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -378,8 +378,8 @@ SPK_API spkadd_status spkadd_numeric(spkadd_handle* h, int64_t* B_col_ptr, int32
                              h->dev, h->st);
   h->launches += cta_items > 0;
   if (ce == cudaSuccess && h->h_ctr.n_warp > 0)
-    ce = spk::launch_num_warp(h->in, f64, h->d_wl, h->h_ctr.n_warp, h->d_s, h->d_u, h->d_colptr, B_row_idx, B_val,
-                              h->opt.warp_max, h->opt.sort_mode, h->d_ctr, h->dev, h->st);
+    ce = spk::launch_num_warp(h->in, f64, h->d_wl, h->d_ctr, h->h_ctr.n_warp, h->d_s, h->d_u, h->d_colptr, B_row_idx,
+                              B_val, h->opt.warp_max, h->opt.sort_mode, h->d_ctr, h->dev, h->st);
   h->launches += h->h_ctr.n_warp > 0;
   if (ce != cudaSuccess) return from_cuda(ce);
   h->state = ST_NUMERIC;

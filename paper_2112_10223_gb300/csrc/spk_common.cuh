@@ -150,22 +150,38 @@ struct ChunkMap {
   int beg;          // this lane's segment begin (fast path)
   int total;
   int L;
+  int shift;        // log2(L) when L is a power of two, else -1
   uint64_t magic;   // ceil(2^32 / L): e / L == (e * magic) >> 32 for e < 2^16, L <= 2^16
+  uint32_t magic32; // the same as a 32-bit factor: e / L == umulhi(e, magic32) (2 <= L < 2^16)
   bool equal;
 
   __device__ __forceinline__ void init(int beg_, int len, int lane, int nvalid) {
     beg = beg_;
     const int L0 = __shfl_sync(SPK_FULL, len, 0);
-    equal = __all_sync(SPK_FULL, lane >= nvalid || len == L0) && L0 > 0 && L0 <= 65536 &&
+    equal = __all_sync(SPK_FULL, lane >= nvalid || len == L0) && L0 >= 2 && L0 < 65536 &&
             (int64_t)L0 * nvalid < 65536;
     if (equal) {
       L = L0;
       total = L0 * nvalid;
+      shift = (L0 & (L0 - 1)) == 0 ? __ffs(L0) - 1 : -1;
       magic = (0xFFFFFFFFull / (uint64_t)L0) + 1ull;
+      magic32 = (uint32_t)magic;
     } else {
       w.init(beg_, len, lane);
       total = w.total;
     }
+  }
+  // Segment of flattened position e and the position's offset inside that
+  // segment.  Every lane must call it (it may shuffle).
+  __device__ __forceinline__ int seg_off(int e, int* off) const {
+    if (equal) {
+      const int sg = shift >= 0 ? (e >> shift) : (int)(((uint64_t)(uint32_t)e * magic) >> 32);
+      *off = e - sg * L;
+      return sg;
+    }
+    const int sg = w.find(e);
+    *off = e - __shfl_sync(SPK_FULL, w.P, sg);
+    return sg;
   }
   // Element index (inside its input) of flattened position e; *seg = segment.
   // Every lane must call it (it shuffles).
@@ -238,8 +254,103 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, in
   return lo;
 }
 
-// Values: fp64 and fp32 shared-memory accumulation.
-template <typename V>
-__device__ __forceinline__ void smem_add(V* p, V v) { atomicAdd(p, v); }
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async, per thread, 4 or 8 bytes):
+// the copy engine fills shared memory while the warp works on other data.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_val(double* dst, const double* src) { cp_async_8(dst, src); }
+__device__ __forceinline__ void cp_async_val(float* dst, const float* src) { cp_async_4(dst, src); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Order-preserving bucket of a row: floor(r * mul / 2^32), mul = floor(2^32 * NB / m)
+// (clamped below 2^32), so buckets are monotone in r and < NB for r < m.
+__device__ __forceinline__ uint32_t bucket_hi(int32_t r, uint32_t mul) {
+  return __umulhi(static_cast<uint32_t>(r), mul);
+}
+
+// Warp-wide exclusive scan of n 32-bit counters (n a multiple of 32) in place;
+// returns the total.
+__device__ __forceinline__ int warp_scan32(uint32_t* c, int n, int lane) {
+  const int per = n >> 5;
+  const int w0 = lane * per;
+  int loc = 0;
+  for (int t = 0; t < per; ++t) loc += (int)c[w0 + t];
+  const int inc = warp_incl_scan(loc, lane);
+  int run = inc - loc;
+  for (int t = 0; t < per; ++t) {
+    const int x = (int)c[w0 + t];
+    c[w0 + t] = (uint32_t)run;
+    run += x;
+  }
+  return __shfl_sync(SPK_FULL, inc, 31);
+}
+
+// ---------------------------------------------------------------------------
+// Staging of one column for a warp: the k input segments of column j are
+// copied (cp.async) into shared memory in flattened order, rows to rk and,
+// when VALS, values to rv.  "Resident" mode (k <= 32): lane l keeps input l's
+// pointers for the whole kernel and the caller prefetched (beg, len) of the
+// column; otherwise the column pointers are read here, 32 inputs at a time.
+// Returns s_j, the number of staged entries (warp-uniform).  The caller
+// commits and waits for the copies.
+// ---------------------------------------------------------------------------
+template <typename V, bool VALS>
+__device__ __forceinline__ void stage_copy(const ChunkMap& cm, const int32_t* ri, const V* va, int32_t* rk, V* rv,
+                                           int lane) {
+  for (int e0 = 0; e0 < cm.total; e0 += 32) {
+    const int e = e0 + lane;
+    int seg;
+    const int idx = cm.locate(e, &seg);
+    const int32_t* rp = reinterpret_cast<const int32_t*>(
+        __shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(ri), seg & 31));
+    const V* vp = nullptr;
+    if constexpr (VALS) vp = reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(va), seg & 31));
+    if (e < cm.total) {
+      cp_async_4(rk + e, rp + idx);
+      if constexpr (VALS) cp_async_val(rv + e, vp + idx);
+    }
+  }
+}
+
+template <typename V, bool VALS>
+__device__ __forceinline__ int stage_column(const Inputs& in, int j, bool resident, int r_beg, int r_len,
+                                            const int32_t* my_ri, const V* my_va, int32_t* rk, V* rv, int lane) {
+  if (resident) {
+    ChunkMap cm;
+    cm.init(r_beg, r_len, lane, in.k);
+    stage_copy<V, VALS>(cm, my_ri, my_va, rk, rv, lane);
+    return cm.total;
+  }
+  int off = 0;
+  for (int cb = 0; cb < in.k; cb += 32) {
+    const int i = cb + lane;
+    int beg = 0, len = 0;
+    const int32_t* ri = nullptr;
+    const V* va = nullptr;
+    if (i < in.k) {
+      const int32_t* cp = in.cp[i];
+      beg = __ldg(cp + j);
+      len = __ldg(cp + j + 1) - beg;
+      ri = in.ri[i];
+      if constexpr (VALS) va = static_cast<const V*>(in.val[i]);
+    }
+    ChunkMap cm;
+    cm.init(beg, len, lane, min(32, in.k - cb));
+    stage_copy<V, VALS>(cm, ri, va, rk + off, rv + (VALS ? off : 0), lane);
+    off += cm.total;
+  }
+  return off;
+}
 
 }  // namespace spk

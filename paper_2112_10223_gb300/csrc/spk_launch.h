@@ -40,9 +40,10 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counte
                              int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
                              const DeviceInfo& dev, cudaStream_t st);
 
-cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, int n_cols, const int32_t* s,
-                            const int32_t* u, const int64_t* col_ptr, int32_t* out_row, void* out_val,
-                            int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
+cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, const Counters* ctr, int n_cols,
+                            const int32_t* s, const int32_t* u, const int64_t* col_ptr, int32_t* out_row,
+                            void* out_val, int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev,
+                            cudaStream_t st);
 cudaError_t launch_num_cta(const Inputs& in, bool f64, const Window* win, int n_win, const int32_t* offs,
                            const int64_t* col_ptr, int32_t* out_row, void* out_val, int window_max,
                            Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);

@@ -12,7 +12,7 @@
 // Alg. 5): occupied slots are compacted, bucketed by an order-preserving map
 // of the row onto [rmin, rmax], placed by a counting sort and ranked inside
 // their bucket.  Warp-class columns use a bucketed, order-preserving hash
-// instead (see k_num_warp), which makes the sort step a counting placement.
+// instead (spk_warp.cu), which makes the sort step a counting placement.
 #include "spk_common.cuh"
 #include "spk_launch.h"
 
@@ -94,169 +94,6 @@ __device__ __forceinline__ int table_insert(int32_t* keys, uint32_t h, uint32_t 
     h = (h + 1) & mask;
   }
   return -1;
-}
-
-// Warp class (s_j <= warp_max): one warp per column.  The table is a bucketed
-// hash with the order-preserving hash b(r) = floor(r * NB / m), NB = 2^q >= s_j
-// buckets: pass 1 counts the entries per bucket, an exclusive scan turns the
-// counts into bucket starts, pass 2 re-reads the entries (now from L1) and
-// places each in its bucket's slot range.  Buckets hold about one entry, so a
-// row's output position is the number of smaller rows in buckets before its
-// own (the scan) plus those in its own bucket (a short comparison loop).  When
-// the symbolic pass found no repeated row in the column (u_j == s_j) this is
-// the whole numeric step: no addition, no atomic on a value.  Otherwise the
-// first copy of each row in its bucket is the leader: it sums the copies and
-// its position discounts the non-leaders before it.
-template <typename V, int WARPS, int U>
-__global__ void __launch_bounds__(WARPS * 32) k_num_warp(Inputs in, const int32_t* __restrict__ list, int ncols,
-                                                         const int32_t* __restrict__ s_arr,
-                                                         const int32_t* __restrict__ u_arr,
-                                                         const int64_t* __restrict__ col_ptr,
-                                                         int32_t* __restrict__ out_row, V* __restrict__ out_val,
-                                                         int smax, int force_dedup, Counters* ctr_w) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const size_t per_warp = ((size_t)smax * (sizeof(V) + 9) + 15) & ~(size_t)15;
-  unsigned char* base = sm_raw + (size_t)wid * per_warp;
-  V* sval = reinterpret_cast<V*>(base);
-  int32_t* skey = reinterpret_cast<int32_t*>(sval + smax);
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(skey + smax);  // smax 16-bit bucket counters
-  uint32_t* aux = cnt + smax / 2;                               // smax 16-bit non-leader counters
-  uint8_t* lead = reinterpret_cast<uint8_t*>(aux + smax / 2);
-  for (int c = blockIdx.x * WARPS + wid; c < ncols; c += gridDim.x * WARPS) {
-    const int j = list[c];
-    const int s = s_arr[j];
-    const int u = u_arr[j];
-    const int64_t out = col_ptr[j];
-    const int qb = max(5, ceil_log2(s));
-    const int NB = 1 << qb;
-    if (NB > smax) continue;  // not reachable for a warp-class column
-    for (int p = lane; p < NB / 2; p += 32) cnt[p] = 0u;
-    __syncwarp();
-    // Pass 1: bucket histogram.
-    for (int cb = 0; cb < in.k; cb += 32) {
-      const int i = cb + lane;
-      int beg = 0, len = 0;
-      if (i < in.k) {
-        const int32_t* cp = in.cp[i];
-        beg = __ldg(cp + j);
-        len = __ldg(cp + j + 1) - beg;
-      }
-      ChunkMap cm;
-      cm.init(beg, len, lane, min(32, in.k - cb));
-      for (int e0 = 0; e0 < cm.total; e0 += 32 * U) {
-        int32_t r[U];
-#pragma unroll
-        for (int t = 0; t < U; ++t) {
-          const int e = e0 + t * 32 + lane;
-          int seg;
-          const int idx = cm.locate(e, &seg);
-          r[t] = -1;
-          if (e < cm.total) r[t] = __ldg(in.ri[cb + seg] + idx);
-        }
-#pragma unroll
-        for (int t = 0; t < U; ++t)
-          if (r[t] >= 0) add16(cnt, hash_ordered(r[t], in.home_mul, qb) & (uint32_t)(NB - 1));
-      }
-    }
-    __syncwarp();
-    warp_scan16(cnt, NB, lane);
-    __syncwarp();
-    // Pass 2: place every entry in its bucket (cnt becomes the bucket ends).
-    for (int cb = 0; cb < in.k; cb += 32) {
-      const int i = cb + lane;
-      int beg = 0, len = 0;
-      if (i < in.k) {
-        const int32_t* cp = in.cp[i];
-        beg = __ldg(cp + j);
-        len = __ldg(cp + j + 1) - beg;
-      }
-      ChunkMap cm;
-      cm.init(beg, len, lane, min(32, in.k - cb));
-      for (int e0 = 0; e0 < cm.total; e0 += 32 * U) {
-        int32_t r[U];
-        V v[U];
-#pragma unroll
-        for (int t = 0; t < U; ++t) {
-          const int e = e0 + t * 32 + lane;
-          int seg;
-          const int idx = cm.locate(e, &seg);
-          r[t] = -1;
-          v[t] = V(0);
-          if (e < cm.total) {
-            r[t] = __ldg(in.ri[cb + seg] + idx);
-            v[t] = __ldg(val_ptr<V>(in, cb + seg) + idx);
-          }
-        }
-#pragma unroll
-        for (int t = 0; t < U; ++t)
-          if (r[t] >= 0) {
-            const int pos = (int)add16(cnt, hash_ordered(r[t], in.home_mul, qb) & (uint32_t)(NB - 1));
-            if (pos < s) {
-              skey[pos] = r[t];
-              sval[pos] = v[t];
-            }
-          }
-      }
-    }
-    __syncwarp();
-    if (!force_dedup && u == s) {
-      for (int p = lane; p < s; p += 32) {
-        const int32_t key = skey[p];
-        const uint32_t b = hash_ordered(key, in.home_mul, qb) & (uint32_t)(NB - 1);
-        const int lo = b ? (int)get16(cnt, b - 1u) : 0;
-        const int hi = (int)get16(cnt, b);
-        int rank = lo;
-        for (int y = lo; y < hi; ++y) rank += skey[y] < key;
-        out_row[out + rank] = key;
-        out_val[out + rank] = sval[p];
-      }
-    } else {
-      for (int p = lane; p < NB / 2; p += 32) aux[p] = 0u;
-      __syncwarp();
-      int nlead = 0;
-      for (int p = lane; p < s; p += 32) {
-        const int32_t key = skey[p];
-        const uint32_t b = hash_ordered(key, in.home_mul, qb) & (uint32_t)(NB - 1);
-        const int lo = b ? (int)get16(cnt, b - 1u) : 0;
-        bool first = true;
-        for (int y = lo; y < p; ++y) first &= skey[y] != key;
-        lead[p] = first;
-        nlead += first;
-        if (!first) add16(aux, b);
-      }
-      nlead = warp_sum(nlead);
-      if (nlead != u) {  // symbolic and numeric disagree: report, write nothing
-        if (lane == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
-        __syncwarp();
-        continue;
-      }
-      __syncwarp();
-      warp_scan16(aux, NB, lane);
-      __syncwarp();
-      for (int p = lane; p < s; p += 32) {
-        if (!lead[p]) continue;
-        const int32_t key = skey[p];
-        const uint32_t b = hash_ordered(key, in.home_mul, qb) & (uint32_t)(NB - 1);
-        const int lo = b ? (int)get16(cnt, b - 1u) : 0;
-        const int hi = (int)get16(cnt, b);
-        int below = 0;
-        V sum = sval[p];
-        for (int y = lo; y < hi; ++y) {
-          const int32_t ky = skey[y];
-          if (ky == key) {
-            if (y != p) sum += sval[y];
-          } else if (ky < key && lead[y]) {
-            ++below;
-          }
-        }
-        const int rank = lo - (int)get16(aux, b) + below;
-        out_row[out + rank] = key;
-        out_val[out + rank] = sum;
-      }
-    }
-    __syncwarp();
-  }
 }
 
 // One thread block per work item: a CTA-class column or a heavy column's row
@@ -415,37 +252,6 @@ static int blocks_per_sm(const DeviceInfo& dev, size_t smem_per_block, int threa
   if (b > bt) b = bt;
   if (b > 32) b = 32;
   return b < 1 ? 1 : b;
-}
-
-template <typename V>
-static cudaError_t launch_num_warp_t(const Inputs& in, const int32_t* list, int n_cols, const int32_t* s,
-                                     const int32_t* u, const int64_t* col_ptr, int32_t* out_row, void* out_val,
-                                     int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev,
-                                     cudaStream_t st) {
-  constexpr int WARPS = 8;
-  const int smax = pow2_at_least(warp_max) < 32 ? 32 : pow2_at_least(warp_max);
-  const size_t per_warp = ((size_t)smax * (sizeof(V) + 9) + 15) & ~(size_t)15;
-  const size_t smem = (size_t)WARPS * per_warp;
-  auto kern = k_num_warp<V, WARPS, 8>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int grid = dev.sms * blocks_per_sm(dev, smem, WARPS * 32);
-  const int need = (n_cols + WARPS - 1) / WARPS;
-  if (grid > need) grid = need;
-  if (grid < 1) return cudaSuccess;
-  kern<<<grid, WARPS * 32, smem, st>>>(in, list, n_cols, s, u, col_ptr, out_row, static_cast<V*>(out_val), smax,
-                                       force_dedup, ctr_w);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, int n_cols, const int32_t* s,
-                            const int32_t* u, const int64_t* col_ptr, int32_t* out_row, void* out_val,
-                            int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
-  if (n_cols <= 0) return cudaSuccess;
-  return f64 ? launch_num_warp_t<double>(in, list, n_cols, s, u, col_ptr, out_row, out_val, warp_max, force_dedup,
-                                         ctr_w, dev, st)
-             : launch_num_warp_t<float>(in, list, n_cols, s, u, col_ptr, out_row, out_val, warp_max, force_dedup,
-                                        ctr_w, dev, st);
 }
 
 template <typename V>

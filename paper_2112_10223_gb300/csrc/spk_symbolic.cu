@@ -1,9 +1,6 @@
 // spk_symbolic.cu -- a2 of the hot path: nnz(B(:,j)) per column.
 //
-// Warp class (s_j <= warp_max): one warp per column, a shared-memory
-//   open-addressing table of keys only (Alg. 6 HashSymbolic), size a power of
-//   two >= 4 s_j, scrambled multiplicative hash, linear probing, atomicCAS on
-//   the row key.
+// Warp class (s_j <= warp_max): see spk_warp.cu.
 // CTA class (s_j <= cta_max): one thread block per column, same table with the
 //   scrambled (multiplicative) hash.  Emits one numeric work item per column.
 // Heavy class: one thread block per column with a shared-memory bitmap of a
@@ -16,76 +13,6 @@
 #include "spk_launch.h"
 
 namespace spk {
-
-template <int WARPS, int U>
-__global__ void __launch_bounds__(WARPS * 32) k_sym_warp(Inputs in, const int32_t* __restrict__ list,
-                                                         const int32_t* __restrict__ s_arr,
-                                                         const Counters* __restrict__ ctr,
-                                                         int32_t* __restrict__ u_out, int tmax, Counters* ctr_w) {
-  extern __shared__ int32_t sm_keys[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int32_t* keys = sm_keys + wid * tmax;
-  const int ncols = ctr->n_warp;
-  int n_unique = 0;
-  for (int c = blockIdx.x * WARPS + wid; c < ncols; c += gridDim.x * WARPS) {
-    const int j = list[c];
-    const int s = s_arr[j];
-    // Table of 2^q >= 4 s_j slots: load factor <= 1/4 keeps the probe loops of
-    // the 32 lanes short and alike.
-    const int q = max(6, ceil_log2(4 * s));
-    const int T = 1 << q;
-    if (T > tmax) {  // cannot happen for a warp-class column; guard the shared table
-      if (lane == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
-      continue;
-    }
-    for (int p = lane; p < T; p += 32) keys[p] = -1;
-    __syncwarp();
-    int newc = 0;
-    for (int cb = 0; cb < in.k; cb += 32) {
-      const int i = cb + lane;
-      int beg = 0, len = 0;
-      if (i < in.k) {
-        const int32_t* cp = in.cp[i];
-        beg = __ldg(cp + j);
-        len = __ldg(cp + j + 1) - beg;
-      }
-      ChunkMap cm;
-      cm.init(beg, len, lane, min(32, in.k - cb));
-      for (int e0 = 0; e0 < cm.total; e0 += 32 * U) {
-        int32_t r[U];
-#pragma unroll
-        for (int t = 0; t < U; ++t) {
-          const int e = e0 + t * 32 + lane;
-          int seg;
-          const int idx = cm.locate(e, &seg);
-          r[t] = -1;
-          if (e < cm.total) r[t] = __ldg(in.ri[cb + seg] + idx);
-        }
-#pragma unroll
-        for (int t = 0; t < U; ++t) {
-          if (r[t] < 0) continue;
-          uint32_t h = hash_scrambled(r[t], q);
-          for (int probes = 0; probes < T; ++probes) {  // T > s_j keys: an empty slot is always found
-            const int old = atomicCAS(&keys[h], -1, r[t]);
-            if (old == -1) {
-              ++newc;
-              break;
-            }
-            if (old == r[t]) break;
-            h = (h + 1) & (T - 1);
-          }
-        }
-      }
-    }
-    newc = warp_sum(newc);
-    if (lane == 0) {
-      u_out[j] = newc;
-      n_unique += (newc == s);
-    }
-    __syncwarp();
-  }
-  if (lane == 0 && n_unique) atomicAdd(&ctr_w->n_unique, n_unique);
-}
 
 template <int BLOCK, int U>
 __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __restrict__ list,
@@ -306,19 +233,6 @@ static int pow2_at_least(int x) {
   int p = 1;
   while (p < x) p <<= 1;
   return p;
-}
-
-cudaError_t launch_sym_warp(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr,
-                            int32_t* u, int warp_max, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
-  constexpr int WARPS = 8;
-  const int tmax = pow2_at_least(4 * warp_max) < 64 ? 64 : pow2_at_least(4 * warp_max);
-  const size_t smem = (size_t)WARPS * tmax * sizeof(int32_t);
-  auto kern = k_sym_warp<WARPS, 8>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int grid = dev.sms * blocks_per_sm(dev, smem, WARPS * 32);
-  kern<<<grid, WARPS * 32, smem, st>>>(in, list, s, ctr, u, tmax, ctr_w);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_sym_cta(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr, int32_t* u,

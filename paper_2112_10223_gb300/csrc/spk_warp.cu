@@ -1,0 +1,447 @@
+// spk_warp.cu -- warp-class columns (s_j = sum_i nnz(A_i(:,j)) <= warp_max):
+// one warp per column, for both the symbolic count (Alg. 6's role) and the
+// numeric sum (Alg. 5's role).
+//
+// The table is a bucketed hash whose hash is order-preserving,
+// b(r) = floor(r * NB / m) with NB = 2^q >= s_j buckets: a bucket holds about
+// one entry and every row of bucket b is smaller than every row of a later
+// bucket.  Insert-or-add by row key happens inside a bucket; the sort of
+// Alg. 5's last step becomes a counting placement plus tiny per-bucket sorts.
+//
+//   pass 1   read the column's rows (coalesced, k segments), count per bucket
+//   scan     exclusive scan of the counts: bucket starts
+//   pass 2   read the rows (and values) again -- they are in L1 now -- and
+//            file every entry at its bucket's next free slot in shared memory
+//   sort     the buckets with two or more entries (listed during the scan)
+//            are insertion-sorted, one per lane; the slots are then the column
+//            sorted by row.  Symbolic: nnz(B(:,j)) = s_j minus the repeated
+//            rows those sorts meet.
+//   finish   numeric: a row's first slot is its leader; it sums its run of
+//            equal rows and writes at (leaders before it).  When the symbolic
+//            pass saw no repeated row (u_j == s_j) the slots are copied out.
+// Output is written in slot order, i.e. row order, so stores coalesce.
+//
+// Entry loads: the k segments of a column are read as one flattened sequence,
+// 32 consecutive positions per warp round (coalesced inside each segment).
+// When every segment has the same length L (Erdos-Renyi and partial-product
+// inputs), position e lies in segment umulhi(e, ceil(2^32/L)); full rounds run
+// without bounds checks.
+#include "spk_common.cuh"
+#include "spk_launch.h"
+
+namespace spk {
+
+// One pad word after every 16 counters: a lane that scans 16 consecutive
+// counters then starts on its own bank (17 l mod 32 is a permutation).
+__device__ __forceinline__ int pad16(int b) { return b + (b >> 4); }
+__host__ __device__ constexpr int padded_words(int n) { return n + (n >> 4) + 1; }
+
+// Per-warp shared memory: values (numeric), row keys, padded bucket counters
+// and the list of buckets holding two or more entries.
+template <typename V, bool NUMERIC>
+__host__ __device__ constexpr size_t warp_col_bytes(int smax) {
+  return ((size_t)smax * ((NUMERIC ? sizeof(V) : 0) + sizeof(int32_t)) +
+          (size_t)padded_words(smax) * sizeof(uint32_t) + (size_t)(smax / 2 + 1) * sizeof(uint32_t) + 15) &
+         ~(size_t)15;
+}
+
+struct WarpColArgs {
+  const int32_t* list;     // warp-class column ids
+  const Counters* ctr;     // n_warp
+  const int32_t* s_arr;    // s_j
+  const int32_t* u_arr;    // numeric: u_j from the symbolic pass
+  const int64_t* col_ptr;  // numeric: B's column pointers
+  int32_t* u_out;          // symbolic: u_j
+  int32_t* out_row;        // numeric: B row indices
+  void* out_val;           // numeric: B values
+  Counters* ctr_w;
+  int smax;
+  int force_dedup;
+};
+
+__device__ __forceinline__ const int32_t* shfl_ptr(const int32_t* p, int src) {
+  return reinterpret_cast<const int32_t*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
+}
+template <typename V>
+__device__ __forceinline__ const V* shfl_vptr(const V* p, int src) {
+  return reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
+}
+
+// Calls f(row, value, valid) for every entry of the chunk (32 inputs at most),
+// lane by lane in flattened order.  Equal-length chunks map positions with one
+// multiply-high and run their full rounds without bounds checks.
+template <bool VALS, int U, typename V, typename F>
+__device__ __forceinline__ void for_each_entry(const ChunkMap& cm, const int32_t* srow, const V* svals, int lane,
+                                               F& f) {
+  if (cm.equal) {
+    const uint32_t M = cm.magic32;
+    const int L = cm.L;
+    const int full = cm.total - cm.total % (32 * U);
+    for (int e0 = 0; e0 < full; e0 += 32 * U) {
+      int32_t r[U];
+      V v[U];
+#pragma unroll
+      for (int t = 0; t < U; ++t) {
+        const int e = e0 + t * 32 + lane;
+        const int sg = (int)__umulhi((uint32_t)e, M);
+        const int off = e - sg * L;
+        r[t] = __ldg(shfl_ptr(srow, sg) + off);
+        if constexpr (VALS) v[t] = __ldg(shfl_vptr(svals, sg) + off);
+      }
+#pragma unroll
+      for (int t = 0; t < U; ++t) f(r[t], v[t], true);
+    }
+    for (int e0 = full; e0 < cm.total; e0 += 32) {
+      const int e = e0 + lane;
+      const bool ok = e < cm.total;
+      const int sg = ok ? (int)__umulhi((uint32_t)e, M) : 0;
+      const int off = e - sg * L;
+      const int32_t* rp = shfl_ptr(srow, sg);
+      int32_t r = -1;
+      V v = V(0);
+      if (ok) r = __ldg(rp + off);
+      if constexpr (VALS) {
+        const V* vp = shfl_vptr(svals, sg);
+        if (ok) v = __ldg(vp + off);
+      }
+      f(r, v, ok);
+    }
+    return;
+  }
+  for (int e0 = 0; e0 < cm.total; e0 += 32 * U) {
+    int32_t r[U];
+    V v[U];
+    bool ok[U];
+#pragma unroll
+    for (int t = 0; t < U; ++t) {
+      const int e = e0 + t * 32 + lane;
+      ok[t] = e < cm.total;
+      const int sg = cm.w.find(e);
+      const int off = e - __shfl_sync(SPK_FULL, cm.w.P, sg);
+      const int32_t* rp = shfl_ptr(srow, sg);
+      r[t] = -1;
+      if (ok[t]) r[t] = __ldg(rp + off);
+      if constexpr (VALS) {
+        const V* vp = shfl_vptr(svals, sg);
+        v[t] = V(0);
+        if (ok[t]) v[t] = __ldg(vp + off);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < U; ++t) f(r[t], v[t], ok[t]);
+  }
+}
+
+// All entries of column j: chunk by chunk of 32 inputs.  Resident mode
+// (k <= 32): the lane's input pointers and (beg, len) come from the caller.
+template <bool VALS, int U, typename V, typename F>
+__device__ __forceinline__ void for_each_column_entry(const Inputs& in, int j, bool resident, int rbeg, int rlen,
+                                                      const int32_t* my_ri, const V* my_va, int lane, F& f) {
+  if (resident) {
+    ChunkMap cm;
+    cm.init(rbeg, rlen, lane, in.k);
+    for_each_entry<VALS, U, V>(cm, my_ri + rbeg, VALS ? my_va + rbeg : my_va, lane, f);
+    return;
+  }
+  for (int cb = 0; cb < in.k; cb += 32) {
+    const int i = cb + lane;
+    int beg = 0, len = 0;
+    const int32_t* ri = nullptr;
+    const V* va = nullptr;
+    if (i < in.k) {
+      const int32_t* cp = in.cp[i];
+      beg = __ldg(cp + j);
+      len = __ldg(cp + j + 1) - beg;
+      ri = in.ri[i] + beg;
+      if constexpr (VALS) va = static_cast<const V*>(in.val[i]) + beg;
+    }
+    ChunkMap cm;
+    cm.init(beg, len, lane, min(32, in.k - cb));
+    for_each_entry<VALS, U, V>(cm, ri, va, lane, f);
+  }
+}
+
+// Exclusive scan of n (a multiple of 32) padded counters; returns the total.
+__device__ __forceinline__ int warp_scan_pad(uint32_t* c, int n, int lane) {
+  const int per = n >> 5;
+  const int b0 = lane * per;
+  int loc = 0;
+  for (int t = 0; t < per; ++t) loc += (int)c[pad16(b0 + t)];
+  const int inc = warp_incl_scan(loc, lane);
+  int run = inc - loc;
+  for (int t = 0; t < per; ++t) {
+    const int p = pad16(b0 + t);
+    const int x = (int)c[p];
+    c[p] = (uint32_t)run;
+    run += x;
+  }
+  return __shfl_sync(SPK_FULL, inc, 31);
+}
+
+// Scalars of one warp-class column, loaded one column ahead of their use.
+struct ColState {
+  int j;    // column id, -1 past the end of the list
+  int beg;  // resident mode: this lane's segment begin
+  int len;  //                and length
+  int s;    // sum of input lengths
+  int u;    // numeric: distinct rows
+  int64_t out;
+};
+
+template <bool NUMERIC>
+__device__ __forceinline__ ColState load_col(const WarpColArgs& a, int cc, int ncols, bool resident,
+                                             const int32_t* my_cp, int lane, int k) {
+  ColState st{-1, 0, 0, 0, 0, 0};
+  if (cc >= ncols) return st;
+  st.j = a.list[cc];
+  st.s = a.s_arr[st.j];
+  if (NUMERIC) {
+    st.u = a.u_arr[st.j];
+    st.out = a.col_ptr[st.j];
+  }
+  if (resident && lane < k) {
+    st.beg = __ldg(my_cp + st.j);
+    st.len = __ldg(my_cp + st.j + 1) - st.beg;
+  }
+  return st;
+}
+
+// Per-entry actions of the three passes.
+template <typename V>
+struct BucketCount {  // pass 1: entries per order-preserving bucket
+  uint32_t* cnt;
+  uint32_t mul;
+  __device__ __forceinline__ void operator()(int32_t r, V, bool ok) {
+    if (ok) atomicAdd(&cnt[pad16((int)bucket_hi(r, mul))], 1u);
+  }
+};
+
+template <typename V, bool NUMERIC>
+struct BucketFile {  // pass 2: file the row (and value) at the bucket's next slot
+  uint32_t* cnt;
+  int32_t* skey;
+  V* sval;
+  uint32_t mul;
+  __device__ __forceinline__ void operator()(int32_t r, V v, bool ok) {
+    if (!ok) return;
+    const uint32_t pos = atomicAdd(&cnt[pad16((int)bucket_hi(r, mul))], 1u);
+    skey[pos] = r;
+    if constexpr (NUMERIC) sval[pos] = v;
+  }
+};
+
+template <typename V, bool NUMERIC, int WARPS, int U>
+__global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ uint32_t s_mul[16];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x < 16) {
+    const uint64_t nb = 1ull << threadIdx.x;
+    s_mul[threadIdx.x] = nb >= (uint64_t)in.m ? 0xFFFFFFFFu : (uint32_t)((nb << 32) / (uint64_t)in.m);
+  }
+  __syncthreads();
+  const int smax = a.smax;
+  unsigned char* base = sm_raw + (size_t)wid * warp_col_bytes<V, NUMERIC>(smax);
+  V* sval = reinterpret_cast<V*>(base);  // numeric only
+  int32_t* skey = reinterpret_cast<int32_t*>(base + (NUMERIC ? (size_t)smax * sizeof(V) : 0));
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(skey + smax);
+  uint32_t* mlist = cnt + padded_words(smax);  // (start | size << 16) of multi-entry buckets
+  const int ncols = a.ctr->n_warp;
+  const bool resident = in.k <= 32;
+  const int32_t* my_cp = nullptr;
+  const int32_t* my_ri = nullptr;
+  const V* my_va = nullptr;
+  if (resident && lane < in.k) {
+    my_cp = in.cp[lane];
+    my_ri = in.ri[lane];
+    if constexpr (NUMERIC) my_va = static_cast<const V*>(in.val[lane]);
+  }
+  int32_t* out_row = a.out_row;
+  V* out_val = static_cast<V*>(a.out_val);
+  const int stride = gridDim.x * WARPS;
+  int c = blockIdx.x * WARPS + wid;
+  // Scalars of the current column and of the next one (loaded a column ahead).
+  ColState cur = load_col<NUMERIC>(a, c, ncols, resident, my_cp, lane, in.k);
+  ColState nxt = load_col<NUMERIC>(a, c + stride, ncols, resident, my_cp, lane, in.k);
+  int n_unique = 0;
+  while (cur.j >= 0) {
+    const int j = cur.j, beg = cur.beg, len = cur.len, s = cur.s, u = cur.u;
+    const int64_t out = cur.out;
+    const int qb = max(5, ceil_log2(s));
+    const int NB = 1 << qb;
+    if (NB > smax) {  // not reachable for a warp-class column
+      if (lane == 0) atomicOr(&a.ctr_w->err, ERR_INTERNAL);
+    } else {
+      const uint32_t mul = s_mul[qb];
+      for (int b = lane; b < padded_words(NB); b += 32) cnt[b] = 0u;
+      __syncwarp();
+      // Pass 1: entries per bucket.
+      BucketCount<V> count{cnt, mul};
+      for_each_column_entry<false, U, V>(in, j, resident, beg, len, my_ri, my_va, lane, count);
+      __syncwarp();
+      // Scan the counts into bucket starts; list the buckets with two or more
+      // entries on the way (they are the only ones that need sorting).
+      int nmulti = 0;
+      {
+        const int per = NB >> 5;
+        const int b0 = lane * per;
+        int loc = 0;
+        for (int t = 0; t < per; ++t) loc += (int)cnt[pad16(b0 + t)];
+        const int inc = warp_incl_scan(loc, lane);
+        int run = inc - loc;
+        for (int t = 0; t < per; ++t) {
+          const int p = pad16(b0 + t);
+          const int x = (int)cnt[p];
+          cnt[p] = (uint32_t)run;
+          const bool multi = x >= 2;
+          const unsigned bal = __ballot_sync(SPK_FULL, multi);
+          if (multi) mlist[nmulti + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)run | ((uint32_t)x << 16);
+          nmulti += __popc(bal);
+          run += x;
+        }
+      }
+      __syncwarp();
+      // Pass 2: file every entry at its bucket's next slot.
+      BucketFile<V, NUMERIC> file{cnt, skey, sval, mul};
+      for_each_column_entry<NUMERIC, U, V>(in, j, resident, beg, len, my_ri, my_va, lane, file);
+      __syncwarp();
+      // Sort the multi-entry buckets, one bucket per lane (insertion sort; they
+      // hold 2-3 entries mostly).  Symbolic: count the repeated rows met.
+      int dups = 0;
+      for (int i = lane; i < nmulti; i += 32) {
+        const uint32_t w = mlist[i];
+        const int lo = (int)(w & 0xffffu), hi = lo + (int)(w >> 16);
+        for (int x = lo + 1; x < hi; ++x) {
+          const int32_t kx = skey[x];
+          V vx;
+          if constexpr (NUMERIC) vx = sval[x];
+          int y = x - 1;
+          while (y >= lo && skey[y] > kx) {
+            skey[y + 1] = skey[y];
+            if constexpr (NUMERIC) sval[y + 1] = sval[y];
+            --y;
+          }
+          skey[y + 1] = kx;
+          if constexpr (NUMERIC) sval[y + 1] = vx;
+        }
+        if constexpr (!NUMERIC)
+          for (int x = lo + 1; x < hi; ++x) dups += skey[x] == skey[x - 1];
+      }
+      __syncwarp();
+      if constexpr (!NUMERIC) {
+        dups = warp_sum(dups);
+        if (lane == 0) {
+          a.u_out[j] = s - dups;
+          n_unique += (dups == 0);
+        }
+      }
+      // The s slots now hold the column's entries sorted by row.  A row's
+      // first slot is its leader; leaders before slot q = ballot prefix.
+      if constexpr (NUMERIC) {
+        if (!a.force_dedup && u == s) {
+          for (int q = lane; q < s; q += 32) {  // no repeated row: copy out
+            out_row[out + q] = skey[q];
+            out_val[out + q] = sval[q];
+          }
+        } else {
+          int before = 0;
+          int32_t carry = -1;  // last row of the previous 32 slots
+          for (int q0 = 0; q0 < s; q0 += 32) {
+            const int q = q0 + lane;
+            const int32_t key = q < s ? skey[q] : -2;
+            int32_t prev = __shfl_up_sync(SPK_FULL, key, 1);
+            if (lane == 0) prev = carry;
+            const bool lead = q < s && key != prev;
+            const unsigned bal = __ballot_sync(SPK_FULL, lead);
+            if (lead) {
+              V sum = sval[q];
+              for (int y = q + 1; y < s && skey[y] == key; ++y) sum += sval[y];
+              const int pos = before + __popc(bal & ((1u << lane) - 1u));
+              if (pos < u) {
+                out_row[out + pos] = key;
+                out_val[out + pos] = sum;
+              }
+            }
+            before += __popc(bal);
+            carry = __shfl_sync(SPK_FULL, key, 31);
+          }
+          if (before != u && lane == 0) atomicOr(&a.ctr_w->err, ERR_INTERNAL);  // symbolic and numeric disagree
+        }
+      }
+    }
+    __syncwarp();
+    c += stride;
+    cur = nxt;
+    nxt = load_col<NUMERIC>(a, c + stride, ncols, resident, my_cp, lane, in.k);
+  }
+  if (!NUMERIC && lane == 0 && n_unique) atomicAdd(&a.ctr_w->n_unique, n_unique);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+static int pow2_at_least(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+static int blocks_per_sm(const DeviceInfo& dev, size_t smem_per_block, int threads_per_block) {
+  const size_t reserve = 1024;
+  int b = (int)(dev.smem_per_sm / (smem_per_block + reserve));
+  int bt = 2048 / threads_per_block;
+  if (b > bt) b = bt;
+  if (b > 32) b = 32;
+  return b < 1 ? 1 : b;
+}
+
+template <typename V, bool NUMERIC>
+static cudaError_t launch_warp_col(const Inputs& in, WarpColArgs a, int warp_max, int n_cols_hint,
+                                   const DeviceInfo& dev, cudaStream_t st) {
+  constexpr int WARPS = 8;
+  a.smax = pow2_at_least(warp_max) < 32 ? 32 : pow2_at_least(warp_max);
+  const size_t smem = (size_t)WARPS * warp_col_bytes<V, NUMERIC>(a.smax);
+  auto kern = k_warp_col<V, NUMERIC, WARPS, NUMERIC ? 8 : 16>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int grid = dev.sms * blocks_per_sm(dev, smem + 128, WARPS * 32);
+  if (n_cols_hint >= 0) {
+    const int need = (n_cols_hint + WARPS - 1) / WARPS;
+    if (grid > need) grid = need;
+    if (grid < 1) return cudaSuccess;
+  }
+  kern<<<grid, WARPS * 32, smem, st>>>(in, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sym_warp(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr,
+                            int32_t* u, int warp_max, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+  WarpColArgs a{};
+  a.list = list;
+  a.ctr = ctr;
+  a.s_arr = s;
+  a.u_out = u;
+  a.ctr_w = ctr_w;
+  return launch_warp_col<int32_t, false>(in, a, warp_max, -1, dev, st);
+}
+
+cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, const Counters* ctr, int n_cols,
+                            const int32_t* s, const int32_t* u, const int64_t* col_ptr, int32_t* out_row,
+                            void* out_val, int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev,
+                            cudaStream_t st) {
+  if (n_cols <= 0) return cudaSuccess;
+  WarpColArgs a{};
+  a.list = list;
+  a.ctr = ctr;
+  a.s_arr = s;
+  a.u_arr = u;
+  a.col_ptr = col_ptr;
+  a.out_row = out_row;
+  a.out_val = out_val;
+  a.ctr_w = ctr_w;
+  a.force_dedup = force_dedup;
+  return f64 ? launch_warp_col<double, true>(in, a, warp_max, n_cols, dev, st)
+             : launch_warp_col<float, true>(in, a, warp_max, n_cols, dev, st);
+}
+
+}  // namespace spk
