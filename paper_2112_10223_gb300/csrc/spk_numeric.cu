@@ -69,6 +69,40 @@ __device__ __forceinline__ void block_scan16(uint32_t* c, int n, int* red) {
     }
 }
 
+// Padded layouts of the thread-block kernel: table slot p lives at sp(p) (one
+// pad slot per 32) and counter word w at cw(w) (one pad word per 4), so a
+// thread that walks a contiguous run of slots or words starts on its own bank.
+__device__ __forceinline__ int sp(int p) { return p + (p >> 5); }
+__host__ __device__ __forceinline__ int cw(int w) { return w + (w >> 2); }
+__device__ __forceinline__ uint32_t get16p(const uint32_t* c, uint32_t h) {
+  return (c[cw((int)(h >> 1))] >> ((h & 1u) << 4)) & 0xffffu;
+}
+__device__ __forceinline__ uint32_t add16p(uint32_t* c, uint32_t h) {
+  const uint32_t sh = (h & 1u) << 4;
+  return (atomicAdd(&c[cw((int)(h >> 1))], 1u << sh) >> sh) & 0xffffu;
+}
+template <int BLOCK>
+__device__ __forceinline__ void block_scan16p(uint32_t* c, int n, int* red) {
+  const int nw = n >> 1;
+  const int per = (nw + BLOCK - 1) / BLOCK;
+  const int w0 = threadIdx.x * per;
+  int loc = 0;
+  for (int t = 0; t < per; ++t)
+    if (w0 + t < nw) {
+      const uint32_t x = c[cw(w0 + t)];
+      loc += (int)(x & 0xffffu) + (int)(x >> 16);
+    }
+  int total;
+  int run = block_excl_scan<BLOCK>(loc, red, &total);
+  for (int t = 0; t < per; ++t)
+    if (w0 + t < nw) {
+      const uint32_t x = c[cw(w0 + t)];
+      const int lo = (int)(x & 0xffffu), hi = (int)(x >> 16);
+      c[cw(w0 + t)] = (uint32_t)run | ((uint32_t)(run + lo) << 16);
+      run += lo + hi;
+    }
+}
+
 // Order-preserving bucket of row r on [rmin, rmin + span): floor((r-rmin)*NB/span).
 __device__ __forceinline__ uint32_t bucket_of(int32_t r, int32_t rmin, uint64_t bmul) {
   return (uint32_t)(((uint64_t)(uint32_t)(r - rmin) * bmul) >> 32);
@@ -77,6 +111,21 @@ __device__ __forceinline__ uint32_t bucket_of(int32_t r, int32_t rmin, uint64_t 
 template <typename V>
 __device__ __forceinline__ const V* val_ptr(const Inputs& in, int i) {
   return static_cast<const V*>(in.val[i]);
+}
+
+// Insert-or-add with the padded slot layout (slot h at sp(h)).
+__device__ __forceinline__ int table_insert_pad(int32_t* keys, uint32_t h, uint32_t mask, int32_t r, bool& fresh) {
+  fresh = false;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int old = atomicCAS(&keys[sp((int)h)], -1, r);
+    if (old == -1) {
+      fresh = true;
+      return (int)h;
+    }
+    if (old == r) return (int)h;
+    h = (h + 1) & mask;
+  }
+  return -1;
 }
 
 // Insert-or-add of (r, v) into the table (Alg. 5, inner loop).  Returns the
@@ -106,17 +155,18 @@ __global__ void __launch_bounds__(BLOCK) k_num_cta(Inputs in, const Window* __re
                                                    Counters* ctr_w) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int red[BLOCK / 32 + 1];
+  __shared__ int s_rng[2];
   constexpr int NW = BLOCK / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   V* vals = reinterpret_cast<V*>(sm_raw);
-  int32_t* keys = reinterpret_cast<int32_t*>(vals + tmax);
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(keys + tmax);  // tmax/2 16-bit counters
+  int32_t* keys = reinterpret_cast<int32_t*>(vals + sp(tmax));
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(keys + sp(tmax));  // tmax/2 16-bit counters, padded
   for (int wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
     const Window W = win[wi];
     const int u = W.u;
     const int j = W.col;
     const int64_t out = col_ptr[j] + W.out_off;
-    const int q = max(6, ceil_log2(2 * u));
+    const int q = max(7, ceil_log2(2 * u));  // >= 64 counters: enough buckets for any span at M = 1
     const int T = 1 << q;
     if (T > tmax || T / BLOCK > SMAX) {
       if (threadIdx.x == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
@@ -124,10 +174,14 @@ __global__ void __launch_bounds__(BLOCK) k_num_cta(Inputs in, const Window* __re
     }
     const uint32_t mask = (uint32_t)T - 1u;
     for (int p = threadIdx.x; p < T; p += BLOCK) {
-      keys[p] = -1;
-      vals[p] = V(0);
+      keys[sp(p)] = -1;
+      vals[sp(p)] = V(0);
     }
-    for (int p = threadIdx.x; p < T / 4; p += BLOCK) cnt[p] = 0u;
+    for (int p = threadIdx.x; p < cw(T / 4); p += BLOCK) cnt[p] = 0u;
+    if (threadIdx.x == 0) {
+      s_rng[0] = INT32_MAX;
+      s_rng[1] = -1;
+    }
     __syncthreads();
     int rmin = INT32_MAX, rmax = -1;
     for (int cb = 0; cb < in.k; cb += 32) {
@@ -165,17 +219,23 @@ __global__ void __launch_bounds__(BLOCK) k_num_cta(Inputs in, const Window* __re
         for (int t = 0; t < U; ++t) {
           if (r[t] < 0) continue;
           bool fresh;
-          const int h = table_insert(keys, hash_scrambled(r[t], q), mask, r[t], fresh);
+          const int h = table_insert_pad(keys, hash_scrambled(r[t], q), mask, r[t], fresh);
           if (h < 0) continue;  // table full: the count check below reports it
-          atomicAdd(&vals[h], v[t]);
+          atomicAdd(&vals[sp(h)], v[t]);
           rmin = min(rmin, r[t]);
           rmax = max(rmax, r[t]);
         }
       }
     }
+    rmin = warp_min(rmin);
+    rmax = warp_max(rmax);
+    if (lane == 0) {
+      atomicMin(&s_rng[0], rmin);
+      atomicMax(&s_rng[1], rmax);
+    }
     __syncthreads();
-    rmin = block_reduce_min<BLOCK>(rmin, red);
-    rmax = block_reduce_max<BLOCK>(rmax, red);
+    rmin = s_rng[0];
+    rmax = s_rng[1];
     // Compaction through registers: thread t owns slots [t*S, t*S + S).
     const int S = T >= BLOCK ? T / BLOCK : 1;
     const int p0 = threadIdx.x * S;
@@ -187,8 +247,8 @@ __global__ void __launch_bounds__(BLOCK) k_num_cta(Inputs in, const Window* __re
       kk[t] = -1;
       vv[t] = V(0);
       if (t < S && p0 + t < T) {
-        kk[t] = keys[p0 + t];
-        vv[t] = vals[p0 + t];
+        kk[t] = keys[sp(p0 + t)];
+        vv[t] = vals[sp(p0 + t)];
         mine += kk[t] >= 0;
       }
     }
@@ -199,8 +259,8 @@ __global__ void __launch_bounds__(BLOCK) k_num_cta(Inputs in, const Window* __re
 #pragma unroll
       for (int t = 0; t < SMAX; ++t)
         if (kk[t] >= 0) {
-          keys[dst] = kk[t];
-          vals[dst] = vv[t];
+          keys[sp(dst)] = kk[t];
+          vals[sp(dst)] = vv[t];
           ++dst;
         }
     } else if (threadIdx.x == 0) {
@@ -211,26 +271,26 @@ __global__ void __launch_bounds__(BLOCK) k_num_cta(Inputs in, const Window* __re
     const int NB = T / 2;
     const uint32_t span = (uint32_t)(rmax - rmin) + 1u;
     const uint64_t bmul = ((uint64_t)NB << 32) / span;
-    for (int x = threadIdx.x; x < u; x += BLOCK) add16(cnt, bucket_of(keys[x], rmin, bmul));
+    for (int x = threadIdx.x; x < u; x += BLOCK) add16p(cnt, bucket_of(keys[sp(x)], rmin, bmul));
     __syncthreads();
-    block_scan16<BLOCK>(cnt, NB, red);
+    block_scan16p<BLOCK>(cnt, NB, red);
     __syncthreads();
     for (int x = threadIdx.x; x < u; x += BLOCK) {
-      const int32_t key = keys[x];
-      const int pos = (int)add16(cnt, bucket_of(key, rmin, bmul));
-      keys[NB + pos] = key;
-      vals[NB + pos] = vals[x];
+      const int32_t key = keys[sp(x)];
+      const int pos = (int)add16p(cnt, bucket_of(key, rmin, bmul));
+      keys[sp(T / 2 + pos)] = key;
+      vals[sp(T / 2 + pos)] = vals[sp(x)];
     }
     __syncthreads();
     for (int x = threadIdx.x; x < u; x += BLOCK) {
-      const int32_t key = keys[NB + x];
+      const int32_t key = keys[sp(T / 2 + x)];
       const uint32_t b = bucket_of(key, rmin, bmul);
-      const int lo = b ? (int)get16(cnt, b - 1u) : 0;
-      const int hi = (int)get16(cnt, b);
+      const int lo = b ? (int)get16p(cnt, b - 1u) : 0;
+      const int hi = (int)get16p(cnt, b);
       int rank = lo;
-      for (int y = lo; y < hi; ++y) rank += keys[NB + y] < key;
+      for (int y = lo; y < hi; ++y) rank += keys[sp(T / 2 + y)] < key;
       out_row[out + rank] = key;
-      out_val[out + rank] = vals[NB + x];
+      out_val[out + rank] = vals[sp(T / 2 + x)];
     }
     __syncthreads();
   }
@@ -261,7 +321,8 @@ static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_w
   constexpr int BLOCK = 512;
   constexpr int SMAX = 2 * WINDOW_MAX_LIMIT / BLOCK;  // 16 slots per thread at the largest table
   const int tmax = pow2_at_least(2 * window_max);
-  const size_t smem = (size_t)tmax * (sizeof(V) + 4) + (size_t)tmax / 2 * 2;
+  const size_t slots = (size_t)tmax + tmax / 32;
+  const size_t smem = slots * (sizeof(V) + 4) + (size_t)cw(tmax / 4) * 4 + 16;
   auto kern = k_num_cta<V, BLOCK, 4, SMAX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

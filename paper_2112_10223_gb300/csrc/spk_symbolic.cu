@@ -95,6 +95,10 @@ __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __r
 }
 
 constexpr int HEAVY_BLOCK = 1024;
+
+// The bitmap keeps one pad word after every 32: a thread that scans 32
+// consecutive words then starts on its own bank.
+__device__ __forceinline__ int bm_pad(int w) { return w + (w >> 5); }
 constexpr int MAX_SLAB_WINDOWS = 1100;  // (2^20 rows / 32 bits per word) / (1024 - 32) + 2
 
 template <int BLOCK, int U>
@@ -120,7 +124,11 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
       const int lo = slab * slab_rows;
       const int hi = (int)min((int64_t)in.m, (int64_t)lo + slab_rows);
       const int words = (hi - lo + 31) >> 5;
-      for (int p = threadIdx.x; p < words; p += BLOCK) bm[p] = 0u;
+      {
+        uint4* bm4 = reinterpret_cast<uint4*>(bm);
+        const int w4 = (bm_pad(words) + 3) >> 2;  // the bitmap buffer is rounded up to whole uint4
+        for (int p = threadIdx.x; p < w4; p += BLOCK) bm4[p] = make_uint4(0u, 0u, 0u, 0u);
+      }
       __syncthreads();
       for (int cb = 0; cb < in.k; cb += 32) {
         const int i = cb + lane;
@@ -151,7 +159,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
 #pragma unroll
           for (int t = 0; t < U; ++t) {
             const int rr = r[t] - lo;
-            if (r[t] >= 0 && rr < hi - lo) atomicOr(&bm[rr >> 5], 1u << (rr & 31));
+            if (r[t] >= 0 && rr < hi - lo) atomicOr(&bm[bm_pad(rr >> 5)], 1u << (rr & 31));
           }
         }
       }
@@ -161,7 +169,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
       const int w0 = threadIdx.x * per;
       int loc = 0;
       for (int t = 0; t < per; ++t)
-        if (w0 + t < words) loc += __popc(bm[w0 + t]);
+        if (w0 + t < words) loc += __popc(bm[bm_pad(w0 + t)]);
       int slab_u;
       const int ex = block_excl_scan<BLOCK>(loc, red, &slab_u);
       const int P = slab_u == 0 ? 0 : (slab_u + win_target - 1) / win_target;
@@ -182,7 +190,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
           const int wd = w0 + t;
           if (wd >= words) break;
           const int before = run;
-          run += __popc(bm[wd]);
+          run += __popc(bm[bm_pad(wd)]);
           const int pb = before / win_target, pa = run / win_target;
           if (pa > pb && pa >= 1 && pa <= P - 1) {
             bnd[pa] = wd + 1;
@@ -254,7 +262,8 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counte
                              const DeviceInfo& dev, cudaStream_t st) {
   const int slab_rows = (int)(in.m < (1 << SLAB_BITS) ? in.m : (1 << SLAB_BITS));
   const int slab_words = (slab_rows + 31) / 32 > 0 ? (slab_rows + 31) / 32 : 1;
-  const size_t smem = (size_t)slab_words * sizeof(uint32_t);
+  const int padded = slab_words + slab_words / 32 + 1;
+  const size_t smem = (size_t)((padded + 3) / 4 * 4) * sizeof(uint32_t);
   auto kern = k_sym_heavy<HEAVY_BLOCK, 4>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
