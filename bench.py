@@ -388,23 +388,285 @@ def run_ours(args, world, rank, local):
     print(json.dumps(out))
 
 
+# ---------------------------------------------------------------------------
+# Batched workload: 4096 independent instances (k log-uniform on [2, 256],
+# m = n log-uniform on [2^10, 2^16], per-column length L_j uniform on
+# [4, 64], half ER / half SpGEMM-like, dtype fp32 or fp64 with probability
+# 1/2, seed 0).  About 1.1e11 input nonzeros in total: more than HBM holds,
+# so instances run in seed order as memory-sized waves, each wave one batch
+# (one set of launches for all its instances).  Compared with one spkadd
+# call per instance on the same inputs.
+# ---------------------------------------------------------------------------
+BATCH_WORKLOAD = "batch4096_k2-256_mn2p10-2p16_L4-64"
+
+
+def _instance_bytes(p):
+    import synth
+
+    sv = 8 if p["dtype"] == torch.float64 else 4
+    nz = synth.instance_nnz_estimate(p)
+    n = p.get("n", p["m"])
+    return 2 * nz * (4 + sv) + 96 * n + 64 * p["k"]  # inputs, B (<= inputs), workspace
+
+
+def plan_waves(params, budget):
+    waves, cur, used = [], [], 0
+    for q, p in enumerate(params):
+        b = _instance_bytes(p)
+        if cur and used + b > budget:
+            waves.append(cur)
+            cur, used = [], 0
+        cur.append(q)
+        used += b
+    if cur:
+        waves.append(cur)
+    return waves
+
+
+def _descriptors(probs):
+    """Flat descriptor arrays of instances whose k inputs are rows of one (k, tot) buffer each."""
+    import numpy as np
+
+    ks, ms, ns, nnz, cps, ris, vas, dts = [], [], [], [], [], [], [], []
+    for A, m in probs:
+        k = len(A)
+        cp, ri, va = A[0]
+        tot = ri.numel()
+        ks.append(k)
+        ms.append(m)
+        ns.append(cp.numel() - 1)
+        dts.append(va.dtype)
+        nnz.append(np.full(k, tot, dtype=np.int64))
+        cps.append(np.full(k, cp.data_ptr(), dtype=np.uint64))
+        ris.append(np.uint64(ri.data_ptr()) + np.arange(k, dtype=np.uint64) * np.uint64(tot * 4))
+        vas.append(np.uint64(va.data_ptr()) + np.arange(k, dtype=np.uint64) * np.uint64(tot * va.element_size()))
+    cat = np.concatenate
+    return dict(k=np.asarray(ks, dtype=np.int32), m=np.asarray(ms), n=np.asarray(ns), nnz=cat(nnz), cp=cat(cps),
+                ri=cat(ris), va=cat(vas), dtypes=dts)
+
+
+def batch_once(spk, desc, dev, stream, options=None):
+    """One batch: plan, symbolic, one flat allocation per output array, numeric, destroy."""
+    import numpy as np
+
+    h = spk.spkadd_batch_plan_raw(desc["k"], desc["m"], desc["n"], desc["nnz"], desc["cp"], desc["ri"], desc["va"],
+                                  desc["dtypes"], stream=stream, options=options)
+    nnz = np.asarray(spk.spkadd_batch_symbolic(h), dtype=np.int64)
+    n1 = desc["n"].astype(np.int64) + 1
+    is64 = np.asarray([d == torch.float64 for d in desc["dtypes"]])
+    cp = torch.empty(int(n1.sum()), dtype=torch.int64, device=dev)
+    ri = torch.empty(max(int(nnz.sum()), 1), dtype=torch.int32, device=dev)
+    v64 = torch.empty(max(int(nnz[is64].sum()), 1), dtype=torch.float64, device=dev)
+    v32 = torch.empty(max(int(nnz[~is64].sum()), 1), dtype=torch.float32, device=dev)
+
+    def offs(sizes):
+        o = np.zeros(sizes.size, dtype=np.uint64)
+        o[1:] = np.cumsum(sizes[:-1]).astype(np.uint64)
+        return o
+
+    a_cp = np.uint64(cp.data_ptr()) + offs(n1) * np.uint64(8)
+    a_ri = np.uint64(ri.data_ptr()) + offs(nnz) * np.uint64(4)
+    a_va = np.zeros(nnz.size, dtype=np.uint64)
+    a_va[is64] = np.uint64(v64.data_ptr()) + offs(nnz[is64]) * np.uint64(8)
+    a_va[~is64] = np.uint64(v32.data_ptr()) + offs(nnz[~is64]) * np.uint64(4)
+    spk.spkadd_batch_numeric_raw(h, a_cp, a_ri, a_va)
+    info = spk.spkadd_get_info(h)
+    spk.spkadd_destroy(h)
+    return (cp, ri, v64, v32, nnz, a_cp, a_ri, a_va), info
+
+
+def run_batch(args, world, rank, local):
+    import numpy as np
+
+    import paper_2112_10223_gb300 as spk
+    import synth
+
+    spk.library()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    params = synth.batch_instance_params(args.batch_count, seed=args.seed + rank)
+    est = np.asarray([synth.instance_nnz_estimate(p) for p in params], dtype=np.float64)
+    edges = np.quantile(est, np.linspace(0, 1, 11))
+    decile = np.clip(np.searchsorted(edges, est, side="right") - 1, 0, 9)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * args.batch_mem_frac)
+    waves = plan_waves(params, budget)
+
+    tot = dict(nnz=0, bytes=0, t_batch=0.0, t_req=0.0, launches=0, instances=0)
+    dec = [dict(instances=0, nnz=0, t_batch=0.0, t_req=0.0) for _ in range(10)]
+    lat_req = []
+    tuned = None
+    tune_log = []
+    verified = 0
+    oracle_nnz, oracle_t, oracle_cores = 0, 0.0, 0
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    for wi, wave in enumerate(waves):
+        probs = [synth.instance(params[q], device=dev) for q in wave]
+        torch.cuda.synchronize()
+        desc = _descriptors(probs)
+        nnz_in = np.asarray([len(A) * A[0][1].numel() for A, _ in probs], dtype=np.int64)
+        if tuned is None:  # pick the class thresholds on the first wave
+            cands = [dict(warp_max=512, cta_max=4096), dict(warp_max=256, cta_max=4096),
+                     dict(warp_max=512, cta_max=2048), dict(warp_max=128, cta_max=1024)]
+            best = None
+            for c in cands:
+                o = spk.default_options(**c)
+                batch_once(spk, desc, dev, stream, o)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                batch_once(spk, desc, dev, stream, o)
+                torch.cuda.synchronize()
+                t = time.perf_counter() - t0
+                tune_log.append(dict(c, ms=t * 1e3))
+                if best is None or t < best[0]:
+                    best = (t, c)
+            tuned = best[1]
+        opt = spk.default_options(**tuned)
+        for _ in range(args.warmup):
+            batch_once(spk, desc, dev, stream, opt)
+        torch.cuda.synchronize()
+        tb = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            res, info = batch_once(spk, desc, dev, stream, opt)
+            torch.cuda.synchronize()
+            tb.append(time.perf_counter() - t0)
+        t_batch = sum(tb) / len(tb)
+        nnz_out = res[4]
+        tot["launches"] += info["kernel_launches"] * args.steps
+        # per-size-decile batches
+        for d in range(10):
+            sel = [i for i, q in enumerate(wave) if decile[q] == d]
+            if not sel:
+                continue
+            sub = _descriptors([probs[i] for i in sel])
+            batch_once(spk, sub, dev, stream, opt)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            batch_once(spk, sub, dev, stream, opt)
+            torch.cuda.synchronize()
+            dec[d]["t_batch"] += time.perf_counter() - t0
+        # one call per instance, in seed order, each waited for
+        spk.spkadd(probs[0][0], probs[0][1])
+        torch.cuda.synchronize()
+        for i, (A, m) in enumerate(probs):
+            t0 = time.perf_counter()
+            spk.spkadd(A, m, options=opt)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            lat_req.append(t)
+            tot["t_req"] += t
+            q = wave[i]
+            dec[decile[q]]["t_req"] += t
+            dec[decile[q]]["instances"] += 1
+            dec[decile[q]]["nnz"] += int(nnz_in[i])
+        # verification of a few instances against the oracle (not timed)
+        if rank == 0 and args.batch_verify > 0:
+            import oracle
+
+            small = sorted(range(len(wave)), key=lambda i: nnz_in[i])
+            picks = small[:1] + [small[len(small) // 2]][: args.batch_verify - 1]
+            cp_all, ri_all, v64, v32 = res[0], res[1], res[2], res[3]
+            for i in picks:
+                if nnz_in[i] > 6e7:
+                    continue
+                A, m = probs[i]
+                An = [tuple(t.cpu().numpy() for t in a) for a in A]
+                t0 = time.perf_counter()
+                want = oracle.add(An)
+                oracle_t += time.perf_counter() - t0
+                oracle_nnz += int(nnz_in[i])
+                oracle_cores = oracle.threads_used(0)
+                n = desc["n"][i]
+                o_cp = int((res[5][i] - np.uint64(cp_all.data_ptr())) // np.uint64(8))
+                o_ri = int((res[6][i] - np.uint64(ri_all.data_ptr())) // np.uint64(4))
+                vbuf = v64 if A[0][2].dtype == torch.float64 else v32
+                o_va = int((res[7][i] - np.uint64(vbuf.data_ptr())) // np.uint64(vbuf.element_size()))
+                nz = int(nnz_out[i])
+                got_cp = cp_all[o_cp:o_cp + n + 1].cpu().numpy()
+                got_ri = ri_all[o_ri:o_ri + nz].cpu().numpy()
+                got_va = vbuf[o_va:o_va + nz].cpu().numpy().astype(np.float64)
+                tol = 1e-12 if A[0][2].dtype == torch.float64 else 1e-5
+                ok = (np.array_equal(got_cp, want["col_ptr"]) and np.array_equal(got_ri, want["row_idx"])
+                      and bool(np.all(np.abs(got_va - want["val"]) <= tol * want["abs_sum"])))
+                if not ok:
+                    raise SystemExit(f"batch parity failed for instance {wave[i]}")
+                verified += 1
+        alg = 0
+        for i, (A, m) in enumerate(probs):
+            sv = A[0][2].element_size()
+            n = A[0][0].numel() - 1
+            alg += algorithmic_bytes(len(A), n, int(nnz_in[i]), int(nnz_out[i]), sv)
+        tot["nnz"] += int(nnz_in.sum())
+        tot["bytes"] += alg
+        tot["t_batch"] += t_batch
+        tot["instances"] += len(wave)
+        del probs, desc, res
+        torch.cuda.empty_cache()
+    clk = clocks.stop() if clocks else None
+    if rank != 0:
+        return
+    peak, peak_src = read_peaks()
+    achieved = tot["bytes"] / tot["t_batch"] / 1e9
+    lat = sorted(lat_req)
+    out = {
+        "metric": METRIC, "value": tot["nnz"] / tot["t_batch"], "unit": "nnz/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot["t_batch"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "instances": tot["instances"], "nnz_in": tot["nnz"],
+                   "waves": len(waves), "wave_budget_bytes": budget, "seed": args.seed,
+                   "l2": "every wave's inputs exceed the 129 MB L2; no flush"},
+        "roofline": {"kernel": "whole batch (all phases)", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                     "algorithmic_bytes": tot["bytes"]},
+        "batch": {
+            "autotune": {"chosen": tuned, "first_wave": tune_log},
+            "instances_per_s": tot["instances"] / tot["t_batch"],
+            "per_request": {"nnz_per_s": tot["nnz"] / tot["t_req"], "instances_per_s": tot["instances"] / tot["t_req"],
+                            "seconds": tot["t_req"], "p50_ms": lat[len(lat) // 2] * 1e3,
+                            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3},
+            "speedup_vs_per_request": tot["t_req"] / tot["t_batch"],
+            "deciles": [{"decile": d, "instances": x["instances"], "nnz_in": x["nnz"],
+                         "batch_ms": x["t_batch"] * 1e3, "per_request_ms": x["t_req"] * 1e3,
+                         "speedup": (x["t_req"] / x["t_batch"]) if x["t_batch"] > 0 else None}
+                        for d, x in enumerate(dec)],
+            "verified_instances": verified,
+        },
+        "cpu_baseline": ({"value": oracle_nnz / oracle_t, "unit": "nnz/s", "cores": oracle_cores, "kind": "oracle",
+                          "sample": f"{verified} verified instances, {oracle_nnz} input nnz, {oracle_t:.2f} s"}
+                         if oracle_t > 0 else None),
+        "e2e": None,
+        "clocks": clk,
+        "gpu_launches": tot["launches"],
+    }
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD], default=DEFAULT_WORKLOAD)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--oracle-cols", type=int, default=1 << 19)
     ap.add_argument("--info", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batched workload")
+    ap.add_argument("--batch-mem-frac", type=float, default=0.55, help="device memory share of one wave")
+    ap.add_argument("--batch-verify", type=int, default=2, help="instances per wave checked against the oracle")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == BATCH_WORKLOAD:
+        run_batch(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -122,7 +122,9 @@ typedef struct spkadd_options {
     void* alloc_ctx;
 } spkadd_options;
 
-/* Planning statistics (host copy), for tests and benchmarks. */
+/* Planning statistics (host copy), for tests and benchmarks.  For a batch
+ * handle k is the total input count, m the largest m and n the total column
+ * count of all problems; the class and window counts cover all problems. */
 typedef struct spkadd_info {
     int64_t k, m, n;
     int64_t nnz_in;         /* sum_i nnz(A_i) */
@@ -135,6 +137,7 @@ typedef struct spkadd_info {
     int64_t cols_unique;    /* warp columns in which no row repeats across the inputs */
     int64_t workspace_bytes;
     int64_t kernel_launches; /* kernels this handle has launched so far */
+    int64_t problems;       /* problems of the handle (1 unless made by spkadd_batch_plan) */
 } spkadd_info;
 
 typedef struct spkadd_handle spkadd_handle;
@@ -176,6 +179,47 @@ spkadd_status spkadd_symbolic(spkadd_handle* h, int64_t* nnz_B);
  * again (with the same or other output buffers) to recompute B.
  */
 spkadd_status spkadd_numeric(spkadd_handle* h, int64_t* B_col_ptr, int32_t* B_row_idx, void* B_val);
+
+/*
+ * Batches.  Many independent SpKAdd problems B_q = A_q,1 + ... + A_q,k_q
+ * (q = 0..count-1, each with its own k, shape and dtype) run as one: every
+ * phase is one set of kernel launches over the columns of all problems,
+ * so the launch count and the host synchronisations do not grow with count.
+ * The paper has no batch interface; its per-column independence (Sec. III:
+ * columns are added independently and in parallel) is what makes one.
+ * Semantics per problem are those of spkadd_plan / spkadd_symbolic /
+ * spkadd_numeric.  Release with spkadd_destroy; spkadd_get_info works too.
+ * spkadd_symbolic and spkadd_numeric reject a batch handle
+ * (SPKADD_ERR_INVALID_ARG); the batch calls accept a handle of spkadd_plan
+ * as a batch of one.
+ *
+ * spkadd_batch_plan
+ *   h       host out: the new handle
+ *   count   number of problems, >= 1
+ *   k       host array of count input counts (1 <= k[q] <= SPKADD_MAX_K)
+ *   A       host array of count pointers; A[q] is a host array of k[q]
+ *           descriptors of problem q (same rules as spkadd_plan's A)
+ *   dtype   host array of count value types
+ *   stream, opt  as for spkadd_plan (the options apply to every problem)
+ * The total input count and the total column count must stay below 2^31
+ * (SPKADD_ERR_OVERFLOW otherwise).  Host checks fail with the first bad
+ * problem's status before any CUDA call.
+ *
+ * spkadd_batch_symbolic
+ *   nnz_B   host out, count entries: nnz(B_q).  Blocks once for the batch.
+ *
+ * spkadd_batch_numeric
+ *   B_col_ptr, B_row_idx, B_val  host arrays of count device pointers:
+ *           problem q's outputs as in spkadd_numeric (B_col_ptr[q] has
+ *           n_q + 1 int64; B_row_idx[q] / B_val[q] may be NULL when
+ *           nnz(B_q) = 0).  The pointer arrays are copied before the call
+ *           returns; the call does not block.
+ */
+spkadd_status spkadd_batch_plan(spkadd_handle** h, int count, const int* k, const spkadd_csc* const* A,
+                                const spkadd_dtype* dtype, void* stream, const spkadd_options* opt);
+spkadd_status spkadd_batch_symbolic(spkadd_handle* h, int64_t* nnz_B);
+spkadd_status spkadd_batch_numeric(spkadd_handle* h, int64_t* const* B_col_ptr, int32_t* const* B_row_idx,
+                                   void* const* B_val);
 
 /* Statistics of the handle (host out).  May synchronise the stream. */
 spkadd_status spkadd_get_info(spkadd_handle* h, spkadd_info* info);

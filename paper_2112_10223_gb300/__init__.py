@@ -15,6 +15,18 @@ Entry points carry the C names:
 row_idx int32[nnz], val float32|float64[nnz])`` CUDA tensors.  ``spkadd(A, m)``
 runs the three phases and returns ``(col_ptr int64, row_idx int32, val)``.
 
+Batches of independent problems (each with its own k, shape and dtype) run
+as one set of launches:
+
+    h = spkadd_batch_plan(problems)          # problems: [(A, m), ...]
+    nnz = spkadd_batch_symbolic(h)           # list, one per problem
+    spkadd_batch_numeric(h, outs)            # outs: [(col_ptr, row_idx, val), ...]
+    spkadd_destroy(h)
+
+``spkadd_batch_plan_raw`` takes the descriptors as flat integer arrays
+instead of tensors (device addresses), for callers that hold many problems
+in packed buffers.
+
 If the library has not been built, every call raises ``SpkaddError``; there
 is no fallback implementation.
 """
@@ -23,6 +35,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 from ._build import LIB_PATH, build  # noqa: F401  (build is re-exported)
@@ -30,7 +43,8 @@ from ._build import LIB_PATH, build  # noqa: F401  (build is re-exported)
 __all__ = [
     "SpkaddError", "Options", "Info", "library", "default_options", "spkadd_plan", "spkadd_symbolic",
     "spkadd_numeric", "spkadd_destroy", "spkadd_get_info", "spkadd_status_string", "spkadd", "Handle",
-    "STATUS", "spkadd_scan_counts_noalloc", "SCAN_NOALLOC_MAX_N",
+    "STATUS", "spkadd_scan_counts_noalloc", "SCAN_NOALLOC_MAX_N", "spkadd_batch_plan", "spkadd_batch_plan_raw",
+    "spkadd_batch_symbolic", "spkadd_batch_numeric", "spkadd_batch_numeric_raw", "spkadd_batch", "BatchHandle",
 ]
 
 SCAN_NOALLOC_MAX_N = 4096 * 4096
@@ -67,7 +81,7 @@ class Options(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "k", "m", "n", "nnz_in", "nnz_out", "cols_warp", "cols_cta", "cols_heavy", "windows", "windows_split",
-        "cols_unique", "workspace_bytes", "kernel_launches")]
+        "cols_unique", "workspace_bytes", "kernel_launches", "problems")]
 
 
 _lib = None
@@ -98,6 +112,12 @@ def library():
         lib.spkadd_status_string.restype = ctypes.c_char_p
         lib.spkadd_version.argtypes = []
         lib.spkadd_version.restype = ctypes.c_int
+        lib.spkadd_batch_plan.argtypes = [ctypes.POINTER(P), ctypes.c_int, P, P, P, P, ctypes.POINTER(Options)]
+        lib.spkadd_batch_plan.restype = ctypes.c_int
+        lib.spkadd_batch_symbolic.argtypes = [P, P]
+        lib.spkadd_batch_symbolic.restype = ctypes.c_int
+        lib.spkadd_batch_numeric.argtypes = [P, P, P, P]
+        lib.spkadd_batch_numeric.restype = ctypes.c_int
         lib.spkadd_scan_counts_noalloc.argtypes = [P, ctypes.c_int64, P, P]
         lib.spkadd_scan_counts_noalloc.restype = ctypes.c_int
         _lib = lib
@@ -245,3 +265,142 @@ def spkadd_scan_counts_noalloc(counts: torch.Tensor, col_ptr: torch.Tensor, stre
     _, sp = _stream_ptr(stream)
     _check(library().spkadd_scan_counts_noalloc(counts.data_ptr() if counts.numel() else None, counts.numel(),
                                                 col_ptr.data_ptr(), sp), "spkadd_scan_counts_noalloc")
+
+
+# ---------------------------------------------------------------------------
+# Batches.
+# ---------------------------------------------------------------------------
+_CSC_NP = np.dtype([("m", np.int64), ("n", np.int64), ("nnz", np.int64), ("col_ptr", np.uint64),
+                    ("row_idx", np.uint64), ("val", np.uint64)])
+assert _CSC_NP.itemsize == ctypes.sizeof(CSC)
+
+
+class BatchHandle(Handle):
+    """A spkadd_handle* of a batch; n and dtype are per-problem lists."""
+
+    def __init__(self, ptr, inputs, ns, dtypes, stream):
+        super().__init__(ptr, inputs, ns, dtypes, stream)
+
+
+def spkadd_batch_plan_raw(k, m, n, nnz, col_ptr, row_idx, val, dtypes, stream=None,
+                          options: Options | None = None, keep=None) -> BatchHandle:
+    """spkadd_batch_plan from flat descriptor arrays.
+
+    k: per-problem input counts (count entries); m, n: per-problem shapes
+    (count entries); nnz, col_ptr, row_idx, val: per-input nnz and device
+    addresses (sum(k) entries, problem by problem); dtypes: per-problem
+    torch.float32 / torch.float64.  `keep` is held by the handle so that the
+    buffers behind the addresses outlive it.
+    """
+    lib = library()
+    k = np.ascontiguousarray(k, dtype=np.int32)
+    count = int(k.size)
+    if count == 0:
+        _check(1, "spkadd_batch_plan")
+    tk = int(k.sum())
+    desc = np.zeros(tk, dtype=_CSC_NP)
+    rep = np.repeat(np.arange(count), k)
+    desc["m"] = np.asarray(m, dtype=np.int64)[rep]
+    desc["n"] = np.asarray(n, dtype=np.int64)[rep]
+    desc["nnz"] = np.asarray(nnz, dtype=np.int64)
+    desc["col_ptr"] = np.asarray(col_ptr, dtype=np.uint64)
+    desc["row_idx"] = np.asarray(row_idx, dtype=np.uint64)
+    desc["val"] = np.asarray(val, dtype=np.uint64)
+    starts = np.concatenate([[0], np.cumsum(k)[:-1]]).astype(np.uint64)
+    ptrs = (np.uint64(desc.ctypes.data) + starts * np.uint64(_CSC_NP.itemsize)).astype(np.uint64)
+    codes = np.asarray([_DTYPE[d] for d in dtypes], dtype=np.int32)
+    stream, sp = _stream_ptr(stream)
+    h = ctypes.c_void_p()
+    _check(lib.spkadd_batch_plan(ctypes.byref(h), count, k.ctypes.data, ptrs.ctypes.data, codes.ctypes.data, sp,
+                                 ctypes.byref(options) if options is not None else None), "spkadd_batch_plan")
+    return BatchHandle(h, keep, [int(x) for x in n], list(dtypes), stream)
+
+
+def spkadd_batch_plan(problems, stream=None, options: Options | None = None) -> BatchHandle:
+    """spkadd_batch_plan over [(A, m), ...], each A a list of (col_ptr, row_idx, val) CUDA tensors."""
+    ks, ms, ns, nnz, cps, ris, vas, dts, keep = [], [], [], [], [], [], [], [], []
+    for q, (A, m) in enumerate(problems):
+        if len(A) == 0:
+            _check(1, "spkadd_batch_plan")
+        dtype = A[0][2].dtype
+        if dtype not in _DTYPE:
+            raise TypeError("values must be float32 or float64")
+        ks.append(len(A))
+        ms.append(int(m))
+        ns.append(A[0][0].numel() - 1)
+        dts.append(dtype)
+        for i, (cp, ri, va) in enumerate(A):
+            for t, dt in ((cp, torch.int32), (ri, torch.int32), (va, dtype)):
+                if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+                    raise TypeError(f"problem {q} input {i}: expected contiguous CUDA tensors (int32, int32, {dtype})")
+            if cp.numel() - 1 != ns[-1]:
+                _check(2, "spkadd_batch_plan")
+            nnz.append(ri.numel())
+            cps.append(cp.data_ptr())
+            ris.append(ri.data_ptr() if ri.numel() else 0)
+            vas.append(va.data_ptr() if va.numel() else 0)
+        keep.append(A)
+    return spkadd_batch_plan_raw(ks, ms, ns, nnz, cps, ris, vas, dts, stream=stream, options=options, keep=keep)
+
+
+def spkadd_batch_symbolic(h: BatchHandle) -> list:
+    """spkadd_batch_symbolic: nnz(B_q) for every problem (blocks once)."""
+    count = len(h.n)
+    out = np.zeros(count, dtype=np.int64)
+    _check(library().spkadd_batch_symbolic(h.ptr, out.ctypes.data), "spkadd_batch_symbolic")
+    h.nnz = [int(x) for x in out]
+    return h.nnz
+
+
+def spkadd_batch_numeric(h: BatchHandle, outs) -> None:
+    """spkadd_batch_numeric: outs[q] = (col_ptr int64[n_q+1], row_idx int32, val) device tensors."""
+    count = len(h.n)
+    if len(outs) != count:
+        raise ValueError("one output triple per problem")
+    cp = np.zeros(count, dtype=np.uint64)
+    ri = np.zeros(count, dtype=np.uint64)
+    va = np.zeros(count, dtype=np.uint64)
+    for q, (c, r, v) in enumerate(outs):
+        if c.dtype != torch.int64 or r.dtype != torch.int32 or v.dtype != h.dtype[q]:
+            raise TypeError(f"problem {q}: B buffers must be int64, int32 and the problem's dtype")
+        if c.numel() != h.n[q] + 1 or (h.nnz is not None and (r.numel() < h.nnz[q] or v.numel() < h.nnz[q])):
+            raise ValueError(f"problem {q}: B buffers too small")
+        cp[q] = c.data_ptr()
+        ri[q] = r.data_ptr() if r.numel() else 0
+        va[q] = v.data_ptr() if v.numel() else 0
+    _check(library().spkadd_batch_numeric(h.ptr, cp.ctypes.data, ri.ctypes.data, va.ctypes.data),
+           "spkadd_batch_numeric")
+
+
+def spkadd_batch_numeric_raw(h: BatchHandle, col_ptr, row_idx, val) -> None:
+    """spkadd_batch_numeric from flat arrays of device addresses (count entries each).
+
+    The caller guarantees the sizes (n_q + 1 int64, nnz_q int32, nnz_q values
+    of problem q's dtype); nothing is checked here beyond the count.
+    """
+    count = len(h.n)
+    cp = np.ascontiguousarray(col_ptr, dtype=np.uint64)
+    ri = np.ascontiguousarray(row_idx, dtype=np.uint64)
+    va = np.ascontiguousarray(val, dtype=np.uint64)
+    if not (cp.size == ri.size == va.size == count):
+        raise ValueError("one address per problem in each array")
+    _check(library().spkadd_batch_numeric(h.ptr, cp.ctypes.data, ri.ctypes.data, va.ctypes.data),
+           "spkadd_batch_numeric")
+
+
+def spkadd_batch(problems, stream=None, options: Options | None = None, info: bool = False):
+    """B_q for every problem [(A, m), ...]; returns a list of (col_ptr, row_idx, val)."""
+    h = spkadd_batch_plan(problems, stream=stream, options=options)
+    try:
+        nnz = spkadd_batch_symbolic(h)
+        outs = []
+        for q, (A, _) in enumerate(problems):
+            dev = A[0][0].device
+            outs.append((torch.empty(h.n[q] + 1, dtype=torch.int64, device=dev),
+                         torch.empty(nnz[q], dtype=torch.int32, device=dev),
+                         torch.empty(nnz[q], dtype=h.dtype[q], device=dev)))
+        spkadd_batch_numeric(h, outs)
+        stats = spkadd_get_info(h) if info else None
+    finally:
+        spkadd_destroy(h)
+    return (outs, stats) if info else outs

@@ -94,9 +94,15 @@ spkadd_status from_device_err(int32_t err) {
 }  // namespace
 
 struct spkadd_handle {
-  int k = 0;
-  int64_t m = 0, n = 0, nnz_in = 0;
-  spkadd_dtype dt = SPKADD_F64;
+  bool batch = false;       // made by spkadd_batch_plan
+  int count = 0;            // problems (1 for spkadd_plan)
+  int total_k = 0;          // inputs of all problems
+  int kmax = 0;
+  int64_t mmax = 0;
+  int64_t ncols = 0;        // columns of all problems
+  int64_t nnz_in = 0;
+  int dt_mode = 0;          // 0 = all float, 1 = all double, 2 = mixed
+  spkadd_dtype dt0 = SPKADD_F64;
   cudaStream_t st = nullptr;
   spkadd_options opt{};
   int device = 0;
@@ -106,7 +112,10 @@ struct spkadd_handle {
   char* offs_buf = nullptr;
   size_t offs_bytes = 0;
   Inputs in{};
-  const int64_t* d_nnz = nullptr;
+  const int64_t* d_nnz = nullptr;      // per (problem, input) nnz
+  int32_t* d_col_inst = nullptr;       // batch: global column -> problem
+  int64_t* d_inst_nnz = nullptr;       // batch: per-problem nnz(B)
+  void** d_out_tab = nullptr;          // batch: B row / value / col_ptr pointer tables
   int32_t *d_s = nullptr, *d_u = nullptr;
   int32_t *d_wl = nullptr, *d_cl = nullptr, *d_hl = nullptr;
   Window* d_win = nullptr;
@@ -118,6 +127,7 @@ struct spkadd_handle {
   int32_t* d_offs = nullptr;
   Counters h_ctr{};
   int64_t nnz_out = -1;
+  std::vector<int64_t> nnz_each;       // batch: per-problem nnz(B) after symbolic
   int state = 0;
   int64_t launches = 0;  // kernels launched by this handle
 
@@ -177,20 +187,12 @@ static spkadd_status check_options(const spkadd_options& o) {
   return SPKADD_OK;
 }
 
-SPK_API spkadd_status spkadd_plan(spkadd_handle** hp, int k, const spkadd_csc* A, spkadd_dtype dtype, void* stream,
-                                  const spkadd_options* opt) {
-  if (!hp) return SPKADD_ERR_INVALID_ARG;
-  *hp = nullptr;
+// Host checks of one problem's descriptors; adds its input count to *nnz.
+static spkadd_status check_problem(int k, const spkadd_csc* A, spkadd_dtype dtype, int64_t* nnz) {
   if (k < 1 || !A) return SPKADD_ERR_INVALID_ARG;
   if (k > SPKADD_MAX_K) return SPKADD_ERR_UNSUPPORTED;
   if (dtype != SPKADD_F32 && dtype != SPKADD_F64) return SPKADD_ERR_INVALID_ARG;
-  spkadd_options o;
-  if (opt) o = *opt;
-  else spkadd_default_options(&o);
-  spkadd_status os = check_options(o);
-  if (os != SPKADD_OK) return os;
   const int64_t m = A[0].m, n = A[0].n;
-  int64_t nnz_in = 0;
   for (int i = 0; i < k; ++i) {
     const spkadd_csc& a = A[i];
     if (a.m < 0 || a.n < 0 || a.nnz < 0) return SPKADD_ERR_INVALID_ARG;
@@ -198,50 +200,94 @@ SPK_API spkadd_status spkadd_plan(spkadd_handle** hp, int k, const spkadd_csc* A
     if (a.m != m || a.n != n) return SPKADD_ERR_SHAPE_MISMATCH;
     if (!a.col_ptr) return SPKADD_ERR_INVALID_ARG;
     if (a.nnz > 0 && (!a.row_idx || !a.val)) return SPKADD_ERR_INVALID_ARG;
-    nnz_in += a.nnz;
+    *nnz += a.nnz;
   }
+  return SPKADD_OK;
+}
+
+// Numeric work items one problem can produce: heavy windows <= nnz /
+// (window_max - 32) + one per heavy column and slab; CTA columns <=
+// min(n, nnz / (warp_max + 1)).
+static int64_t window_bound(int64_t m, int64_t n, int64_t nnz, const spkadd_options& o) {
+  const int64_t slab_rows = (int64_t)1 << spk::SLAB_BITS;
+  const int64_t slabs = m > 0 ? (m + slab_rows - 1) / slab_rows : 1;
+  int64_t heavy_cols = nnz / (o.cta_max + 1);
+  if (heavy_cols > n) heavy_cols = n;
+  int64_t cta_cols = nnz / (o.warp_max + 1);
+  if (cta_cols > n) cta_cols = n;
+  return nnz / (o.window_max - 32) + heavy_cols * (slabs + 1) + cta_cols + 16;
+}
+
+// Plans `count` problems (count = 1 and batch = false for spkadd_plan).
+static spkadd_status plan_problems(spkadd_handle** hp, bool batch, int count, const int* ks,
+                                   const spkadd_csc* const* As, const spkadd_dtype* dts, void* stream,
+                                   const spkadd_options* opt) {
+  if (!hp) return SPKADD_ERR_INVALID_ARG;
+  *hp = nullptr;
+  if (count < 1 || !ks || !As || !dts) return SPKADD_ERR_INVALID_ARG;
+  spkadd_options o;
+  if (opt) o = *opt;
+  else spkadd_default_options(&o);
+  spkadd_status os = check_options(o);
+  if (os != SPKADD_OK) return os;
+  int64_t nnz_in = 0, total_k = 0, ncols = 0, mmax = 0, win_cap = 0;
+  int kmax = 0;
+  bool any32 = false, any64 = false;
+  for (int q = 0; q < count; ++q) {
+    int64_t nz = 0;
+    const spkadd_status ps = check_problem(ks[q], As[q], dts[q], &nz);
+    if (ps != SPKADD_OK) return ps;
+    nnz_in += nz;
+    total_k += ks[q];
+    ncols += As[q][0].n;
+    if (As[q][0].m > mmax) mmax = As[q][0].m;
+    if (ks[q] > kmax) kmax = ks[q];
+    (dts[q] == SPKADD_F64 ? any64 : any32) = true;
+    win_cap += window_bound(As[q][0].m, As[q][0].n, nz, o);
+  }
+  if (total_k >= INT32_MAX || ncols >= INT32_MAX || win_cap >= INT32_MAX) return SPKADD_ERR_OVERFLOW;
 
   spkadd_handle* h = new (std::nothrow) spkadd_handle();
   if (!h) return SPKADD_ERR_NOMEM;
-  h->k = k;
-  h->m = m;
-  h->n = n;
+  h->batch = batch;
+  h->count = count;
+  h->total_k = (int)total_k;
+  h->kmax = kmax;
+  h->mmax = mmax;
+  h->ncols = ncols;
   h->nnz_in = nnz_in;
-  h->dt = dtype;
+  h->dt_mode = any32 && any64 ? 2 : (any64 ? 1 : 0);
+  h->dt0 = dts[0];
   h->st = static_cast<cudaStream_t>(stream);
   h->opt = o;
+  h->win_cap = win_cap;
   cudaError_t ce = cudaGetDevice(&h->device);
   if (ce == cudaSuccess) ce = device_info(h->device, &h->dev);
   if (ce != cudaSuccess) {
     delete h;
     return from_cuda(ce);
   }
-
-  // Window capacity: heavy windows <= nnz_in / (window_max - 32) + one per
-  // heavy column and slab; CTA columns <= min(n, nnz_in / (warp_max + 1)).
-  const int64_t slab_rows = (int64_t)1 << spk::SLAB_BITS;
-  const int64_t slabs = m > 0 ? (m + slab_rows - 1) / slab_rows : 1;
-  int64_t heavy_cols = nnz_in / (o.cta_max + 1);
-  if (heavy_cols > n) heavy_cols = n;
-  int64_t cta_cols = nnz_in / (o.warp_max + 1);
-  if (cta_cols > n) cta_cols = n;
-  h->win_cap = nnz_in / (o.window_max - 32) + heavy_cols * (slabs + 1) + cta_cols + 16;
+  const bool multi = count > 1;
 
   Carver cv;
-  const size_t o_cp = cv.take<const int32_t*>(k);
-  const size_t o_ri = cv.take<const int32_t*>(k);
-  const size_t o_va = cv.take<const void*>(k);
-  const size_t o_nnz = cv.take<int64_t>(k);
+  const size_t o_inst = cv.take<spk::Inst>(count);
+  const size_t o_cp = cv.take<const int32_t*>(total_k);
+  const size_t o_ri = cv.take<const int32_t*>(total_k);
+  const size_t o_va = cv.take<const void*>(total_k);
+  const size_t o_nnz = cv.take<int64_t>(total_k);
   const size_t o_ctr = cv.take<Counters>(1);
-  const size_t o_s = cv.take<int32_t>(n);
-  const size_t o_u = cv.take<int32_t>(n);
-  const size_t o_wl = cv.take<int32_t>(n);
-  const size_t o_cl = cv.take<int32_t>(n);
-  const size_t o_hl = cv.take<int32_t>(n);
-  const size_t o_win = cv.take<Window>(h->win_cap);
-  const size_t o_srch = cv.take<int32_t>(h->win_cap);
-  const size_t o_colp = cv.take<int64_t>(n + 1);
-  const size_t o_scan = cv.take<long long>(spk::scan_tiles(n));
+  const size_t o_out = cv.take<void*>(batch ? 3 * (size_t)count : 0);
+  const size_t o_inz = cv.take<int64_t>(batch ? count : 0);
+  const size_t o_ci = cv.take<int32_t>(multi ? ncols : 0);
+  const size_t o_s = cv.take<int32_t>(ncols);
+  const size_t o_u = cv.take<int32_t>(ncols);
+  const size_t o_wl = cv.take<int32_t>(ncols);
+  const size_t o_cl = cv.take<int32_t>(ncols);
+  const size_t o_hl = cv.take<int32_t>(ncols);
+  const size_t o_win = cv.take<Window>(win_cap);
+  const size_t o_srch = cv.take<int32_t>(win_cap);
+  const size_t o_colp = cv.take<int64_t>(ncols + 1);
+  const size_t o_scan = cv.take<long long>(spk::scan_tiles(ncols));
   h->ws_bytes = align_up(cv.off, 256);
   h->ws = static_cast<char*>(h->dev_alloc(h->ws_bytes));
   if (!h->ws) {
@@ -250,6 +296,9 @@ SPK_API spkadd_status spkadd_plan(spkadd_handle** hp, int k, const spkadd_csc* A
   }
   h->d_nnz = reinterpret_cast<const int64_t*>(h->ws + o_nnz);
   h->d_ctr = reinterpret_cast<Counters*>(h->ws + o_ctr);
+  h->d_out_tab = batch ? reinterpret_cast<void**>(h->ws + o_out) : nullptr;
+  h->d_inst_nnz = batch ? reinterpret_cast<int64_t*>(h->ws + o_inz) : nullptr;
+  h->d_col_inst = multi ? reinterpret_cast<int32_t*>(h->ws + o_ci) : nullptr;
   h->d_s = reinterpret_cast<int32_t*>(h->ws + o_s);
   h->d_u = reinterpret_cast<int32_t*>(h->ws + o_u);
   h->d_wl = reinterpret_cast<int32_t*>(h->ws + o_wl);
@@ -260,31 +309,59 @@ SPK_API spkadd_status spkadd_plan(spkadd_handle** hp, int k, const spkadd_csc* A
   h->d_colptr = reinterpret_cast<int64_t*>(h->ws + o_colp);
   h->d_scan = reinterpret_cast<long long*>(h->ws + o_scan);
 
-  // Descriptor tables (one host staging buffer, one copy).
-  const size_t desc_bytes = o_ctr;  // tables occupy [0, o_ctr)
-  std::vector<char> host(desc_bytes + sizeof(Counters), 0);
-  for (int i = 0; i < k; ++i) {
-    reinterpret_cast<const int32_t**>(host.data() + o_cp)[i] = A[i].col_ptr;
-    reinterpret_cast<const int32_t**>(host.data() + o_ri)[i] = A[i].row_idx;
-    reinterpret_cast<const void**>(host.data() + o_va)[i] = A[i].val;
-    reinterpret_cast<int64_t*>(host.data() + o_nnz)[i] = A[i].nnz;
+  // Problem and pointer tables plus zeroed counters: one host staging
+  // buffer, one copy.
+  const size_t desc_bytes = o_ctr + sizeof(Counters);
+  std::vector<char> host(desc_bytes, 0);
+  spk::Inst* hi = reinterpret_cast<spk::Inst*>(host.data() + o_inst);
+  int ptr = 0, colbase = 0;
+  for (int q = 0; q < count; ++q) {
+    const spkadd_csc* A = As[q];
+    spk::Inst& I = hi[q];
+    I.k = ks[q];
+    I.m = (int32_t)A[0].m;
+    I.n = (int32_t)A[0].n;
+    I.dtype = dts[q] == SPKADD_F64 ? 1 : 0;
+    I.colbase = colbase;
+    I.ptr_off = ptr;
+    for (int b = 0; b < 16; ++b) {
+      const uint64_t nb = 1ull << b;
+      I.bucket_mul[b] = (I.m == 0 || nb >= (uint64_t)I.m) ? 0xFFFFFFFFu : (uint32_t)((nb << 32) / (uint64_t)I.m);
+    }
+    for (int i = 0; i < ks[q]; ++i, ++ptr) {
+      reinterpret_cast<const int32_t**>(host.data() + o_cp)[ptr] = A[i].col_ptr;
+      reinterpret_cast<const int32_t**>(host.data() + o_ri)[ptr] = A[i].row_idx;
+      reinterpret_cast<const void**>(host.data() + o_va)[ptr] = A[i].val;
+      reinterpret_cast<int64_t*>(host.data() + o_nnz)[ptr] = A[i].nnz;
+    }
+    colbase += I.n;
   }
-  ce = cudaMemcpyAsync(h->ws, host.data(), desc_bytes + sizeof(Counters), cudaMemcpyHostToDevice, h->st);
+  ce = cudaMemcpyAsync(h->ws, host.data(), desc_bytes, cudaMemcpyHostToDevice, h->st);
   if (ce != cudaSuccess) {
     spkadd_destroy(h);
     return from_cuda(ce);
   }
+  h->in.inst = reinterpret_cast<const spk::Inst*>(h->ws + o_inst);
+  h->in.col_inst = h->d_col_inst;
   h->in.cp = reinterpret_cast<const int32_t* const*>(h->ws + o_cp);
   h->in.ri = reinterpret_cast<const int32_t* const*>(h->ws + o_ri);
   h->in.val = reinterpret_cast<const void* const*>(h->ws + o_va);
-  h->in.k = k;
-  h->in.m = (int32_t)m;
-  h->in.n = (int32_t)n;
-  h->in.home_mul = m > 0 ? (((uint64_t)1 << 48) / (uint64_t)m) : 0;
+  h->in.ninst = count;
+  h->in.ncols = (int32_t)ncols;
+  h->in.kmax = kmax;
+  h->in.mmax = (int32_t)mmax;
+  if (multi) {
+    ce = spk::launch_col_inst(h->in, h->d_col_inst, h->dev.sms, h->st);
+    h->launches += 1;
+    if (ce != cudaSuccess) {
+      spkadd_destroy(h);
+      return from_cuda(ce);
+    }
+  }
 
   if (o.validate) {
     ce = spk::launch_validate(h->in, h->d_nnz, h->d_ctr, h->dev.sms, h->st);
-    h->launches += n > 0;
+    h->launches += ncols > 0;
     Pinned* pb = pinned_block();
     if (ce == cudaSuccess && !pb) ce = cudaErrorMemoryAllocation;
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&pb->ctr, h->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, h->st);
@@ -301,7 +378,7 @@ SPK_API spkadd_status spkadd_plan(spkadd_handle** hp, int k, const spkadd_csc* A
   }
   ce = spk::launch_bin(h->in, o.warp_max, o.cta_max, h->d_s, h->d_u, h->d_wl, h->d_cl, h->d_hl, h->d_ctr,
                        h->dev.sms, h->st);
-  h->launches += n > 0;
+  h->launches += ncols > 0;
   if (ce != cudaSuccess) {
     spkadd_destroy(h);
     return from_cuda(ce);
@@ -311,15 +388,26 @@ SPK_API spkadd_status spkadd_plan(spkadd_handle** hp, int k, const spkadd_csc* A
   return SPKADD_OK;
 }
 
-SPK_API spkadd_status spkadd_symbolic(spkadd_handle* h, int64_t* nnz_B) {
-  if (!h || !nnz_B) return SPKADD_ERR_INVALID_ARG;
-  if (h->state < ST_PLANNED) return SPKADD_ERR_STATE;
-  if (h->state >= ST_SYMBOLIC) {  // already counted: the workspace holds the result
-    *nnz_B = h->nnz_out;
-    return SPKADD_OK;
-  }
+SPK_API spkadd_status spkadd_plan(spkadd_handle** hp, int k, const spkadd_csc* A, spkadd_dtype dtype, void* stream,
+                                  const spkadd_options* opt) {
+  if (!hp) return SPKADD_ERR_INVALID_ARG;
+  *hp = nullptr;
+  if (k < 1 || !A) return SPKADD_ERR_INVALID_ARG;
+  const spkadd_csc* As[1] = {A};
+  return plan_problems(hp, false, 1, &k, As, &dtype, stream, opt);
+}
+
+SPK_API spkadd_status spkadd_batch_plan(spkadd_handle** hp, int count, const int* k, const spkadd_csc* const* A,
+                                        const spkadd_dtype* dtype, void* stream, const spkadd_options* opt) {
+  return plan_problems(hp, true, count, k, A, dtype, stream, opt);
+}
+
+// The symbolic phase of every problem of the handle; one stream
+// synchronisation.  Fills h->nnz_out (all problems) and, for a batch,
+// h->nnz_each.
+static spkadd_status run_symbolic(spkadd_handle* h) {
   cudaError_t ce = cudaSuccess;
-  if (h->n > 0) {
+  if (h->ncols > 0) {
     ce = spk::launch_sym_heavy(h->in, h->d_hl, h->d_ctr, h->d_u, h->d_win, h->d_search, h->win_cap, h->d_ctr,
                                h->opt.window_max, h->dev, h->st);
     if (ce == cudaSuccess)
@@ -330,13 +418,22 @@ SPK_API spkadd_status spkadd_symbolic(spkadd_handle* h, int64_t* nnz_B) {
                                 h->st);
     h->launches += 3;
   }
-  if (ce == cudaSuccess) ce = spk::launch_scan(h->d_u, (int)h->n, h->d_scan, h->d_colptr, h->st);
-  h->launches += h->n > 0 ? 3 : 2;
+  if (ce == cudaSuccess) ce = spk::launch_scan(h->d_u, (int)h->ncols, h->d_scan, h->d_colptr, h->st);
+  h->launches += h->ncols > 0 ? 3 : 2;
+  if (ce == cudaSuccess && h->batch) {
+    ce = spk::launch_inst_nnz(h->in, h->d_colptr, h->d_inst_nnz, h->st);
+    h->launches += 1;
+  }
   Pinned* pb = pinned_block();
   if (ce == cudaSuccess && !pb) ce = cudaErrorMemoryAllocation;
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(&pb->ctr, h->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, h->st);
   if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(&pb->nnz, h->d_colptr + h->n, sizeof(long long), cudaMemcpyDeviceToHost, h->st);
+    ce = cudaMemcpyAsync(&pb->nnz, h->d_colptr + h->ncols, sizeof(long long), cudaMemcpyDeviceToHost, h->st);
+  if (ce == cudaSuccess && h->batch) {
+    h->nnz_each.assign(h->count, 0);
+    ce = cudaMemcpyAsync(h->nnz_each.data(), h->d_inst_nnz, sizeof(int64_t) * h->count, cudaMemcpyDeviceToHost,
+                         h->st);
+  }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->st);
   if (ce != cudaSuccess) return from_cuda(ce);
   h->h_ctr = pb->ctr;
@@ -347,7 +444,7 @@ SPK_API spkadd_status spkadd_symbolic(spkadd_handle* h, int64_t* nnz_B) {
   // Per-input offsets of split windows (sized now that their count is known).
   const int64_t ns = h->h_ctr.n_search;
   if (ns > 0) {
-    const size_t need = (size_t)ns * h->k * 2 * sizeof(int32_t);
+    const size_t need = (size_t)ns * h->kmax * 2 * sizeof(int32_t);
     if (need > h->offs_bytes) {
       h->dev_free(h->offs_buf);
       h->offs_buf = static_cast<char*>(h->dev_alloc(need));
@@ -360,28 +457,96 @@ SPK_API spkadd_status spkadd_symbolic(spkadd_handle* h, int64_t* nnz_B) {
     h->launches += 1;
   }
   h->state = ST_SYMBOLIC;
+  return SPKADD_OK;
+}
+
+SPK_API spkadd_status spkadd_symbolic(spkadd_handle* h, int64_t* nnz_B) {
+  if (!h || !nnz_B || h->batch) return SPKADD_ERR_INVALID_ARG;
+  if (h->state < ST_PLANNED) return SPKADD_ERR_STATE;
+  if (h->state < ST_SYMBOLIC) {
+    const spkadd_status s = run_symbolic(h);
+    if (s != SPKADD_OK) return s;
+  }
   *nnz_B = h->nnz_out;
   return SPKADD_OK;
 }
 
-SPK_API spkadd_status spkadd_numeric(spkadd_handle* h, int64_t* B_col_ptr, int32_t* B_row_idx, void* B_val) {
-  if (!h || !B_col_ptr) return SPKADD_ERR_INVALID_ARG;
-  if (h->state < ST_SYMBOLIC) return SPKADD_ERR_STATE;
-  if (h->nnz_out > 0 && (!B_row_idx || !B_val)) return SPKADD_ERR_INVALID_ARG;
-  cudaError_t ce = cudaMemcpyAsync(B_col_ptr, h->d_colptr, (size_t)(h->n + 1) * sizeof(int64_t),
-                                   cudaMemcpyDeviceToDevice, h->st);
-  const bool f64 = h->dt == SPKADD_F64;
+SPK_API spkadd_status spkadd_batch_symbolic(spkadd_handle* h, int64_t* nnz_B) {
+  if (!h || !nnz_B) return SPKADD_ERR_INVALID_ARG;
+  if (h->state < ST_PLANNED) return SPKADD_ERR_STATE;
+  if (h->state < ST_SYMBOLIC) {
+    const spkadd_status s = run_symbolic(h);
+    if (s != SPKADD_OK) return s;
+  }
+  if (h->batch) std::memcpy(nnz_B, h->nnz_each.data(), sizeof(int64_t) * h->count);
+  else nnz_B[0] = h->nnz_out;
+  return SPKADD_OK;
+}
+
+// The numeric kernels of every problem, writing through `out`.
+static spkadd_status run_numeric(spkadd_handle* h, const spk::Outs& out) {
+  cudaError_t ce = cudaSuccess;
   const int cta_items = h->h_ctr.n_windows;
-  if (ce == cudaSuccess && cta_items > 0)
-    ce = spk::launch_num_cta(h->in, f64, h->d_win, cta_items, h->d_offs, h->d_colptr, B_row_idx, B_val,
+  if (cta_items > 0)
+    ce = spk::launch_num_cta(h->in, h->dt_mode, h->d_win, cta_items, h->d_offs, h->d_colptr, out,
                              h->opt.window_max > h->opt.cta_max ? h->opt.window_max : h->opt.cta_max, h->d_ctr,
                              h->dev, h->st);
   h->launches += cta_items > 0;
   if (ce == cudaSuccess && h->h_ctr.n_warp > 0)
-    ce = spk::launch_num_warp(h->in, f64, h->d_wl, h->d_ctr, h->h_ctr.n_warp, h->d_s, h->d_u, h->d_colptr, B_row_idx,
-                              B_val, h->opt.warp_max, h->opt.sort_mode, h->d_ctr, h->dev, h->st);
+    ce = spk::launch_num_warp(h->in, h->dt_mode, h->d_wl, h->d_ctr, h->h_ctr.n_warp, h->d_s, h->d_u, h->d_colptr,
+                              out, h->opt.warp_max, h->opt.sort_mode, h->d_ctr, h->dev, h->st);
   h->launches += h->h_ctr.n_warp > 0;
+  return from_cuda(ce);
+}
+
+SPK_API spkadd_status spkadd_numeric(spkadd_handle* h, int64_t* B_col_ptr, int32_t* B_row_idx, void* B_val) {
+  if (!h || !B_col_ptr || h->batch) return SPKADD_ERR_INVALID_ARG;
+  if (h->state < ST_SYMBOLIC) return SPKADD_ERR_STATE;
+  if (h->nnz_out > 0 && (!B_row_idx || !B_val)) return SPKADD_ERR_INVALID_ARG;
+  cudaError_t ce = cudaMemcpyAsync(B_col_ptr, h->d_colptr, (size_t)(h->ncols + 1) * sizeof(int64_t),
+                                   cudaMemcpyDeviceToDevice, h->st);
   if (ce != cudaSuccess) return from_cuda(ce);
+  spk::Outs out{};
+  out.row0 = B_row_idx;
+  out.val0 = B_val;
+  out.cp0 = B_col_ptr;
+  const spkadd_status s = run_numeric(h, out);
+  if (s != SPKADD_OK) return s;
+  h->state = ST_NUMERIC;
+  return SPKADD_OK;
+}
+
+SPK_API spkadd_status spkadd_batch_numeric(spkadd_handle* h, int64_t* const* B_col_ptr, int32_t* const* B_row_idx,
+                                           void* const* B_val) {
+  if (!h || !B_col_ptr || !B_row_idx || !B_val) return SPKADD_ERR_INVALID_ARG;
+  if (h->state < ST_SYMBOLIC) return SPKADD_ERR_STATE;
+  if (!h->batch) return spkadd_numeric(h, B_col_ptr[0], B_row_idx[0], B_val[0]);
+  const int n = h->count;
+  std::vector<void*> tab(3 * (size_t)n);
+  for (int q = 0; q < n; ++q) {
+    if (!B_col_ptr[q]) return SPKADD_ERR_INVALID_ARG;
+    if (h->nnz_each[q] > 0 && (!B_row_idx[q] || !B_val[q])) return SPKADD_ERR_INVALID_ARG;
+    tab[q] = B_row_idx[q];
+    tab[n + q] = B_val[q];
+    tab[2 * (size_t)n + q] = B_col_ptr[q];
+  }
+  // Pageable source: the call returns once the table is staged, so `tab`
+  // may go out of scope right after.
+  cudaError_t ce =
+      cudaMemcpyAsync(h->d_out_tab, tab.data(), sizeof(void*) * tab.size(), cudaMemcpyHostToDevice, h->st);
+  if (ce != cudaSuccess) return from_cuda(ce);
+  spk::Outs out{};
+  out.row0 = B_row_idx[0];
+  out.val0 = B_val[0];
+  out.cp0 = B_col_ptr[0];
+  out.rows = reinterpret_cast<int32_t* const*>(h->d_out_tab);
+  out.vals = reinterpret_cast<void* const*>(h->d_out_tab + n);
+  out.cps = reinterpret_cast<int64_t* const*>(h->d_out_tab + 2 * (size_t)n);
+  ce = spk::launch_out_colptr(h->in, out, h->d_colptr, h->dev.sms, h->st);
+  h->launches += 1;
+  if (ce != cudaSuccess) return from_cuda(ce);
+  const spkadd_status s = run_numeric(h, out);
+  if (s != SPKADD_OK) return s;
   h->state = ST_NUMERIC;
   return SPKADD_OK;
 }
@@ -389,9 +554,10 @@ SPK_API spkadd_status spkadd_numeric(spkadd_handle* h, int64_t* B_col_ptr, int32
 SPK_API spkadd_status spkadd_get_info(spkadd_handle* h, spkadd_info* info) {
   if (!h || !info) return SPKADD_ERR_INVALID_ARG;
   std::memset(info, 0, sizeof(*info));
-  info->k = h->k;
-  info->m = h->m;
-  info->n = h->n;
+  info->k = h->total_k;
+  info->m = h->mmax;
+  info->n = h->ncols;
+  info->problems = h->count;
   info->nnz_in = h->nnz_in;
   info->nnz_out = h->state >= ST_SYMBOLIC ? h->nnz_out : -1;
   Pinned* pb = pinned_block();

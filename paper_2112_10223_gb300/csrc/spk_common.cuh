@@ -41,17 +41,46 @@ struct Counters {
   int32_t pad;
 };
 
-// Inputs as the kernels see them (device pointer tables of length k).
+// One SpKAdd problem of a batch, as the kernels see it.  A single call is a
+// batch of one.  Columns of all problems are numbered in one global column
+// space: problem q owns global columns [colbase, colbase + n), and B's entries
+// of problem q sit at global col_ptr_B positions minus col_ptr_B[colbase].
+struct Inst {
+  int32_t k, m, n, dtype;   // dtype: 0 = float, 1 = double
+  int32_t colbase;          // first global column
+  int32_t ptr_off;          // first (problem, input) entry of the pointer tables
+  uint32_t bucket_mul[16];  // floor(2^32 * 2^q / m), clamped below 2^32, q = 0..15
+};
+
 struct Inputs {
-  const int32_t* const* cp;
+  const Inst* inst;
+  const int32_t* col_inst;  // global column -> problem (nullptr for a batch of one)
+  const int32_t* const* cp; // pointer tables, one entry per (problem, input)
   const int32_t* const* ri;
   const void* const* val;
-  int32_t k;
-  int32_t m;
-  int32_t n;
-  int32_t pad;
-  uint64_t home_mul;    // floor(2^48 / m): order-preserving home slot factor
+  int32_t ninst;
+  int32_t ncols;            // total columns of all problems
+  int32_t kmax;
+  int32_t mmax;
 };
+
+__device__ __forceinline__ int inst_of(const Inputs& in, int g) { return in.col_inst ? __ldg(in.col_inst + g) : 0; }
+
+// Where B goes: the caller's buffers, through per-problem pointer tables
+// (rows/vals/cps, a batch) or directly (row0/val0/cp0: a single problem, and
+// problem 0 of any batch, so a batch of one may use either).  Row/value positions inside a problem's
+// buffers are global col_ptr_B values minus col_ptr_B[colbase].
+struct Outs {
+  int32_t* row0;
+  void* val0;
+  int64_t* cp0;
+  int32_t* const* rows;
+  void* const* vals;
+  int64_t* const* cps;
+};
+__device__ __forceinline__ int32_t* out_row_of(const Outs& o, int q) { return o.rows ? o.rows[q] : o.row0; }
+__device__ __forceinline__ void* out_val_of(const Outs& o, int q) { return o.vals ? o.vals[q] : o.val0; }
+__device__ __forceinline__ int64_t* out_cp_of(const Outs& o, int q) { return o.cps ? o.cps[q] : o.cp0; }
 
 // ---------------------------------------------------------------------------
 // Hash functions.  The paper hashes with (a * r) & (2^q - 1), a prime
@@ -61,12 +90,6 @@ struct Inputs {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t hash_scrambled(int32_t r, int q) {
   return (static_cast<uint32_t>(r) * 0x9E3779B1u) >> (32 - q);
-}
-
-// Order-preserving home slot: floor(r * 2^q / m) (computed as
-// (r * floor(2^48/m)) >> (48 - q)); monotone in r, always < 2^q.
-__device__ __forceinline__ uint32_t hash_ordered(int32_t r, uint64_t home_mul, int q) {
-  return static_cast<uint32_t>((static_cast<uint64_t>(static_cast<uint32_t>(r)) * home_mul) >> (48 - q));
 }
 
 __device__ __forceinline__ int ceil_log2(int x) {  // x >= 1
@@ -254,25 +277,6 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, in
   return lo;
 }
 
-// ---------------------------------------------------------------------------
-// Asynchronous global -> shared copies (cp.async, per thread, 4 or 8 bytes):
-// the copy engine fills shared memory while the warp works on other data.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void cp_async_4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_val(double* dst, const double* src) { cp_async_8(dst, src); }
-__device__ __forceinline__ void cp_async_val(float* dst, const float* src) { cp_async_4(dst, src); }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
 // Order-preserving bucket of a row: floor(r * mul / 2^32), mul = floor(2^32 * NB / m)
 // (clamped below 2^32), so buckets are monotone in r and < NB for r < m.
 __device__ __forceinline__ uint32_t bucket_hi(int32_t r, uint32_t mul) {
@@ -294,63 +298,6 @@ __device__ __forceinline__ int warp_scan32(uint32_t* c, int n, int lane) {
     run += x;
   }
   return __shfl_sync(SPK_FULL, inc, 31);
-}
-
-// ---------------------------------------------------------------------------
-// Staging of one column for a warp: the k input segments of column j are
-// copied (cp.async) into shared memory in flattened order, rows to rk and,
-// when VALS, values to rv.  "Resident" mode (k <= 32): lane l keeps input l's
-// pointers for the whole kernel and the caller prefetched (beg, len) of the
-// column; otherwise the column pointers are read here, 32 inputs at a time.
-// Returns s_j, the number of staged entries (warp-uniform).  The caller
-// commits and waits for the copies.
-// ---------------------------------------------------------------------------
-template <typename V, bool VALS>
-__device__ __forceinline__ void stage_copy(const ChunkMap& cm, const int32_t* ri, const V* va, int32_t* rk, V* rv,
-                                           int lane) {
-  for (int e0 = 0; e0 < cm.total; e0 += 32) {
-    const int e = e0 + lane;
-    int seg;
-    const int idx = cm.locate(e, &seg);
-    const int32_t* rp = reinterpret_cast<const int32_t*>(
-        __shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(ri), seg & 31));
-    const V* vp = nullptr;
-    if constexpr (VALS) vp = reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(va), seg & 31));
-    if (e < cm.total) {
-      cp_async_4(rk + e, rp + idx);
-      if constexpr (VALS) cp_async_val(rv + e, vp + idx);
-    }
-  }
-}
-
-template <typename V, bool VALS>
-__device__ __forceinline__ int stage_column(const Inputs& in, int j, bool resident, int r_beg, int r_len,
-                                            const int32_t* my_ri, const V* my_va, int32_t* rk, V* rv, int lane) {
-  if (resident) {
-    ChunkMap cm;
-    cm.init(r_beg, r_len, lane, in.k);
-    stage_copy<V, VALS>(cm, my_ri, my_va, rk, rv, lane);
-    return cm.total;
-  }
-  int off = 0;
-  for (int cb = 0; cb < in.k; cb += 32) {
-    const int i = cb + lane;
-    int beg = 0, len = 0;
-    const int32_t* ri = nullptr;
-    const V* va = nullptr;
-    if (i < in.k) {
-      const int32_t* cp = in.cp[i];
-      beg = __ldg(cp + j);
-      len = __ldg(cp + j + 1) - beg;
-      ri = in.ri[i];
-      if constexpr (VALS) va = static_cast<const V*>(in.val[i]);
-    }
-    ChunkMap cm;
-    cm.init(beg, len, lane, min(32, in.k - cb));
-    stage_copy<V, VALS>(cm, ri, va, rk + off, rv + (VALS ? off : 0), lane);
-    off += cm.total;
-  }
-  return off;
 }
 
 }  // namespace spk

@@ -8,6 +8,7 @@
 namespace spk {
 
 struct Inputs;
+struct Outs;
 struct Counters;
 struct Window;
 
@@ -25,6 +26,8 @@ struct DeviceInfo {
 
 cudaError_t launch_bin(const Inputs& in, int warp_max, int cta_max, int32_t* s, int32_t* u, int32_t* warp_list,
                        int32_t* cta_list, int32_t* heavy_list, Counters* ctr, int sms, cudaStream_t st);
+// Batch: col_inst[colbase + j] = q for every column j of every problem q.
+cudaError_t launch_col_inst(const Inputs& in, int32_t* col_inst, int sms, cudaStream_t st);
 cudaError_t launch_validate(const Inputs& in, const int64_t* nnz, Counters* ctr, int sms, cudaStream_t st);
 size_t scan_tiles(int64_t n);
 cudaError_t launch_scan(const int32_t* u, int n, long long* tile_buf, int64_t* col_ptr, cudaStream_t st);
@@ -40,12 +43,16 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counte
                              int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
                              const DeviceInfo& dev, cudaStream_t st);
 
-cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, const Counters* ctr, int n_cols,
-                            const int32_t* s, const int32_t* u, const int64_t* col_ptr, int32_t* out_row,
-                            void* out_val, int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev,
-                            cudaStream_t st);
-cudaError_t launch_num_cta(const Inputs& in, bool f64, const Window* win, int n_win, const int32_t* offs,
-                           const int64_t* col_ptr, int32_t* out_row, void* out_val, int window_max,
-                           Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
+// dt: 0 = every problem float, 1 = every problem double, 2 = mixed batch.
+cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const Counters* ctr, int n_cols,
+                            const int32_t* s, const int32_t* u, const int64_t* col_ptr, const Outs& out,
+                            int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
+cudaError_t launch_num_cta(const Inputs& in, int dt, const Window* win, int n_win, const int32_t* offs,
+                           const int64_t* col_ptr, const Outs& out, int window_max, Counters* ctr_w,
+                           const DeviceInfo& dev, cudaStream_t st);
+// Per-problem column pointers of B (a batch): out_cp[q][j] = col_ptr[colbase + j] - col_ptr[colbase].
+cudaError_t launch_out_colptr(const Inputs& in, const Outs& o, const int64_t* col_ptr, int sms, cudaStream_t st);
+// Per-problem nnz(B): nnz[q] = col_ptr[colbase + n] - col_ptr[colbase].
+cudaError_t launch_inst_nnz(const Inputs& in, const int64_t* col_ptr, int64_t* nnz, cudaStream_t st);
 
 }  // namespace spk

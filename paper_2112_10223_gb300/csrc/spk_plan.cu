@@ -19,20 +19,24 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t* __restrict__ lis
 }
 
 // a1 of the hot path: s_j = sum_i nnz(A_i(:,j)) and the column's class
-// (Sec. III-A: the symbolic phase balances load on the summed input count).
+// (Sec. III-A: the symbolic phase balances load on the summed input count),
+// for every global column of every problem of the batch.
 __global__ void __launch_bounds__(256) k_bin(Inputs in, int warp_max, int cta_max, int32_t* __restrict__ s_out,
                                              int32_t* __restrict__ u_out, int32_t* __restrict__ warp_list,
                                              int32_t* __restrict__ cta_list, int32_t* __restrict__ heavy_list,
                                              Counters* __restrict__ ctr) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < in.n; j0 += stride) {
-    const int j = (int)(j0 + threadIdx.x);
-    const bool live = j < in.n;
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < in.ncols; g0 += stride) {
+    const int g = (int)(g0 + threadIdx.x);
+    const bool live = g < in.ncols;
     int64_t s = 0;
     if (live) {
-      for (int i = 0; i < in.k; ++i) {
-        const int32_t* cp = in.cp[i];
+      const Inst* I = in.inst + inst_of(in, g);
+      const int k = __ldg(&I->k), off = __ldg(&I->ptr_off);
+      const int j = g - __ldg(&I->colbase);
+      for (int i = 0; i < k; ++i) {
+        const int32_t* cp = in.cp[off + i];
         s += (int64_t)__ldg(cp + j + 1) - (int64_t)__ldg(cp + j);
       }
     }
@@ -46,12 +50,20 @@ __global__ void __launch_bounds__(256) k_bin(Inputs in, int warp_max, int cta_ma
       else if (s <= warp_max) cls = CLS_WARP;
       else if (s <= cta_max) cls = CLS_CTA;
       else cls = CLS_HEAVY;
-      s_out[j] = (int32_t)s;
-      if (cls == CLS_EMPTY) u_out[j] = 0;
+      s_out[g] = (int32_t)s;
+      if (cls == CLS_EMPTY) u_out[g] = 0;
     }
-    warp_append(cls == CLS_WARP, warp_list, &ctr->n_warp, j, lane);
-    warp_append(cls == CLS_CTA, cta_list, &ctr->n_cta, j, lane);
-    warp_append(cls == CLS_HEAVY, heavy_list, &ctr->n_heavy, j, lane);
+    warp_append(cls == CLS_WARP, warp_list, &ctr->n_warp, g, lane);
+    warp_append(cls == CLS_CTA, cta_list, &ctr->n_cta, g, lane);
+    warp_append(cls == CLS_HEAVY, heavy_list, &ctr->n_heavy, g, lane);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_col_inst(const Inst* __restrict__ inst, int ninst,
+                                                  int32_t* __restrict__ col_inst) {
+  for (int q = blockIdx.x; q < ninst; q += gridDim.x) {
+    const int cb = inst[q].colbase, n = inst[q].n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) col_inst[cb + j] = q;
   }
 }
 
@@ -60,21 +72,25 @@ __global__ void __launch_bounds__(256) k_bin(Inputs in, int warp_max, int cta_ma
 __global__ void __launch_bounds__(256) k_validate(Inputs in, const int64_t* __restrict__ nnz, Counters* ctr) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int err = 0;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < in.n; j += stride) {
-    for (int i = 0; i < in.k; ++i) {
-      const int32_t* cp = in.cp[i];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < in.ncols; g += stride) {
+    const Inst* I = in.inst + inst_of(in, (int)g);
+    const int k = I->k, off = I->ptr_off, m = I->m, n = I->n;
+    const int64_t j = g - I->colbase;
+    for (int i = 0; i < k; ++i) {
+      const int32_t* cp = in.cp[off + i];
       const int64_t b = __ldg(cp + j), e = __ldg(cp + j + 1);
+      const int64_t nz = nnz[off + i];
       if (j == 0 && b != 0) err |= ERR_RANGE;
-      if (j == in.n - 1 && e != nnz[i]) err |= ERR_RANGE;
-      if (b < 0 || e < b || e > nnz[i]) {
+      if (j == n - 1 && e != nz) err |= ERR_RANGE;
+      if (b < 0 || e < b || e > nz) {
         err |= ERR_RANGE;
         continue;
       }
-      const int32_t* ri = in.ri[i];
+      const int32_t* ri = in.ri[off + i];
       int32_t prev = -1;
       for (int64_t p = b; p < e; ++p) {
         const int32_t r = __ldg(ri + p);
-        if (r < 0 || r >= in.m) err |= ERR_RANGE;
+        if (r < 0 || r >= m) err |= ERR_RANGE;
         if (r <= prev) err |= ERR_UNSORTED;
         prev = r;
       }
@@ -177,22 +193,50 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_apply(const int32_t* __rest
 
 // Per-input offsets of split row windows (Sec. III-B: "partition rows ...
 // using binary searches"): for window w and input i, the first entry of
-// A_i(:,col) with row >= r_lo and the first with row >= r_hi.
+// A_i(:,col) with row >= r_lo and the first with row >= r_hi.  Rows of the
+// offset table are kmax inputs wide.
 __global__ void __launch_bounds__(256) k_window_search(Inputs in, const Window* __restrict__ win,
                                                        const int32_t* __restrict__ search_list, int n_search,
                                                        int32_t* __restrict__ offs) {
-  const int64_t total = (int64_t)n_search * in.k;
+  const int64_t total = (int64_t)n_search * in.kmax;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
-    const int s = (int)(t / in.k), i = (int)(t - (int64_t)s * in.k);
+    const int s = (int)(t / in.kmax), i = (int)(t - (int64_t)s * in.kmax);
     const Window w = win[search_list[s]];
-    const int32_t* cp = in.cp[i];
-    const int b = __ldg(cp + w.col), e = __ldg(cp + w.col + 1);
-    const int32_t* ri = in.ri[i];
+    const Inst* I = in.inst + inst_of(in, w.col);
+    if (i >= I->k) continue;
+    const int j = w.col - I->colbase;
+    const int32_t* cp = in.cp[I->ptr_off + i];
+    const int b = __ldg(cp + j), e = __ldg(cp + j + 1);
+    const int32_t* ri = in.ri[I->ptr_off + i];
     const int lo = lower_bound_i32(ri, b, e, w.r_lo);
     const int hi = lower_bound_i32(ri, lo, e, w.r_hi);
     offs[2 * t] = lo;
     offs[2 * t + 1] = hi;
+  }
+}
+
+// B's column pointers per problem: out_cp[j] = col_ptr[colbase + j] - col_ptr[colbase].
+__global__ void __launch_bounds__(256) k_out_colptr(Inputs in, Outs o, const int64_t* __restrict__ col_ptr) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < (int64_t)in.ncols + in.ninst; g += stride) {
+    if (g < in.ncols) {
+      const int q = inst_of(in, (int)g);
+      const int cb = in.inst[q].colbase;
+      out_cp_of(o, q)[g - cb] = col_ptr[g] - col_ptr[cb];
+    } else {  // the closing entry of problem q
+      const int q = (int)(g - in.ncols);
+      const Inst& I = in.inst[q];
+      out_cp_of(o, q)[I.n] = col_ptr[I.colbase + I.n] - col_ptr[I.colbase];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_inst_nnz(Inputs in, const int64_t* __restrict__ col_ptr,
+                                                  int64_t* __restrict__ nnz) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < in.ninst; q += gridDim.x * blockDim.x) {
+    const Inst& I = in.inst[q];
+    nnz[q] = col_ptr[I.colbase + I.n] - col_ptr[I.colbase];
   }
 }
 
@@ -201,16 +245,23 @@ __global__ void __launch_bounds__(256) k_window_search(Inputs in, const Window* 
 // ---------------------------------------------------------------------------
 cudaError_t launch_bin(const Inputs& in, int warp_max, int cta_max, int32_t* s, int32_t* u, int32_t* wl, int32_t* cl,
                        int32_t* hl, Counters* ctr, int sms, cudaStream_t st) {
-  if (in.n == 0) return cudaSuccess;
-  int64_t blocks = ((int64_t)in.n + 255) / 256;
+  if (in.ncols == 0) return cudaSuccess;
+  int64_t blocks = ((int64_t)in.ncols + 255) / 256;
   if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
   k_bin<<<(int)blocks, 256, 0, st>>>(in, warp_max, cta_max, s, u, wl, cl, hl, ctr);
   return cudaGetLastError();
 }
 
+cudaError_t launch_col_inst(const Inputs& in, int32_t* col_inst, int sms, cudaStream_t st) {
+  int blocks = in.ninst < sms * 8 ? in.ninst : sms * 8;
+  if (blocks < 1) return cudaSuccess;
+  k_col_inst<<<blocks, 256, 0, st>>>(in.inst, in.ninst, col_inst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_validate(const Inputs& in, const int64_t* nnz, Counters* ctr, int sms, cudaStream_t st) {
-  if (in.n == 0) return cudaSuccess;
-  int64_t blocks = ((int64_t)in.n + 255) / 256;
+  if (in.ncols == 0) return cudaSuccess;
+  int64_t blocks = ((int64_t)in.ncols + 255) / 256;
   if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
   k_validate<<<(int)blocks, 256, 0, st>>>(in, nnz, ctr);
   return cudaGetLastError();
@@ -230,10 +281,24 @@ cudaError_t launch_scan(const int32_t* u, int n, long long* tile_buf, int64_t* c
 cudaError_t launch_window_search(const Inputs& in, const Window* win, const int32_t* search_list, int n_search,
                                  int32_t* offs, int sms, cudaStream_t st) {
   if (n_search <= 0) return cudaSuccess;
-  int64_t total = (int64_t)n_search * in.k;
+  int64_t total = (int64_t)n_search * in.kmax;
   int64_t blocks = (total + 255) / 256;
   if (blocks > (int64_t)sms * 32) blocks = (int64_t)sms * 32;
   k_window_search<<<(int)blocks, 256, 0, st>>>(in, win, search_list, n_search, offs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inst_nnz(const Inputs& in, const int64_t* col_ptr, int64_t* nnz, cudaStream_t st) {
+  const int blocks = (in.ninst + 255) / 256;
+  k_inst_nnz<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(in, col_ptr, nnz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_out_colptr(const Inputs& in, const Outs& o, const int64_t* col_ptr, int sms, cudaStream_t st) {
+  int64_t blocks = ((int64_t)in.ncols + in.ninst + 255) / 256;
+  if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+  if (blocks < 1) blocks = 1;
+  k_out_colptr<<<(int)blocks, 256, 0, st>>>(in, o, col_ptr);
   return cudaGetLastError();
 }
 

@@ -25,8 +25,10 @@ __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __r
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ncols = ctr->n_cta;
   for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
-    const int j = list[c];
-    const int s = s_arr[j];
+    const int g = list[c];
+    const Inst* I = in.inst + inst_of(in, g);
+    const int k = I->k, off = I->ptr_off, j = g - I->colbase;
+    const int s = s_arr[g];
     const int q = max(6, ceil_log2(2 * s));
     const int T = 1 << q;
     if (T > tmax) {
@@ -36,11 +38,11 @@ __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __r
     for (int p = threadIdx.x; p < T; p += BLOCK) keys[p] = -1;
     __syncthreads();
     int newc = 0;
-    for (int cb = 0; cb < in.k; cb += 32) {
+    for (int cb = 0; cb < k; cb += 32) {
       const int i = cb + lane;
       int beg = 0, len = 0;
-      if (i < in.k) {
-        const int32_t* cp = in.cp[i];
+      if (i < k) {
+        const int32_t* cp = in.cp[off + i];
         beg = __ldg(cp + j);
         len = __ldg(cp + j + 1) - beg;
       }
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __r
           const int seg = w.find(e);
           const int idx = w.index_in_input(e, seg);
           r[t] = -1;
-          if (e < w.total) r[t] = __ldg(in.ri[cb + seg] + idx);
+          if (e < w.total) r[t] = __ldg(in.ri[off + cb + seg] + idx);
         }
 #pragma unroll
         for (int t = 0; t < U; ++t) {
@@ -75,13 +77,13 @@ __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __r
     int total;
     block_excl_scan<BLOCK>(newc, red, &total);
     if (threadIdx.x == 0) {
-      u_out[j] = total;
+      u_out[g] = total;
       const int wi = atomicAdd(&ctr_w->n_windows, 1);
       if (wi < win_cap) {
         Window w;
-        w.col = j;
+        w.col = g;
         w.r_lo = 0;
-        w.r_hi = in.m;
+        w.r_hi = I->m;
         w.u = total;
         w.out_off = 0;
         w.search = -1;
@@ -116,13 +118,15 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ncols = ctr->n_heavy;
   const int slab_rows = slab_words * 32;
-  const int nslabs = (int)(((int64_t)in.m + slab_rows - 1) / slab_rows);
   for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
-    const int j = list[c];
+    const int g = list[c];
+    const Inst* I = in.inst + inst_of(in, g);
+    const int k = I->k, off = I->ptr_off, m = I->m, j = g - I->colbase;
+    const int nslabs = (int)(((int64_t)m + slab_rows - 1) / slab_rows);
     if (threadIdx.x == 0) s_col_u = 0;
     for (int slab = 0; slab < nslabs; ++slab) {
       const int lo = slab * slab_rows;
-      const int hi = (int)min((int64_t)in.m, (int64_t)lo + slab_rows);
+      const int hi = (int)min((int64_t)m, (int64_t)lo + slab_rows);
       const int words = (hi - lo + 31) >> 5;
       {
         uint4* bm4 = reinterpret_cast<uint4*>(bm);
@@ -130,14 +134,14 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
         for (int p = threadIdx.x; p < w4; p += BLOCK) bm4[p] = make_uint4(0u, 0u, 0u, 0u);
       }
       __syncthreads();
-      for (int cb = 0; cb < in.k; cb += 32) {
+      for (int cb = 0; cb < k; cb += 32) {
         const int i = cb + lane;
         int beg = 0, len = 0;
-        if (i < in.k) {
-          const int32_t* cp = in.cp[i];
+        if (i < k) {
+          const int32_t* cp = in.cp[off + i];
           int b = __ldg(cp + j), e = __ldg(cp + j + 1);
           if (nslabs > 1) {
-            const int32_t* ri = in.ri[i];
+            const int32_t* ri = in.ri[off + i];
             b = lower_bound_i32(ri, b, e, lo);
             e = lower_bound_i32(ri, b, e, hi);
           }
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
             const int seg = w.find(e);
             const int idx = w.index_in_input(e, seg);
             r[t] = -1;
-            if (e < w.total) r[t] = __ldg(in.ri[cb + seg] + idx);
+            if (e < w.total) r[t] = __ldg(in.ri[off + cb + seg] + idx);
           }
 #pragma unroll
           for (int t = 0; t < U; ++t) {
@@ -203,9 +207,9 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
           const int wi = s_wbase + p;
           if (wi < win_cap && (whole || s_sbase + p < win_cap)) {
             Window w;
-            w.col = j;
+            w.col = g;
             w.r_lo = whole ? 0 : lo + 32 * bnd[p];
-            w.r_hi = whole ? in.m : (int)min((int64_t)hi, (int64_t)lo + 32 * (int64_t)bnd[p + 1]);
+            w.r_hi = whole ? m : (int)min((int64_t)hi, (int64_t)lo + 32 * (int64_t)bnd[p + 1]);
             w.u = cval[p + 1] - cval[p];
             w.out_off = col_u + cval[p];
             w.search = whole ? -1 : s_sbase + p;
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
       if (threadIdx.x == 0) s_col_u += slab_u;
       __syncthreads();
     }
-    if (threadIdx.x == 0) u_out[j] = s_col_u;
+    if (threadIdx.x == 0) u_out[g] = s_col_u;
     __syncthreads();
   }
 }
@@ -260,7 +264,7 @@ cudaError_t launch_sym_cta(const Inputs& in, const int32_t* list, const int32_t*
 cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counters* ctr, int32_t* u, Window* win,
                              int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
                              const DeviceInfo& dev, cudaStream_t st) {
-  const int slab_rows = (int)(in.m < (1 << SLAB_BITS) ? in.m : (1 << SLAB_BITS));
+  const int slab_rows = (int)(in.mmax < (1 << SLAB_BITS) ? in.mmax : (1 << SLAB_BITS));
   const int slab_words = (slab_rows + 31) / 32 > 0 ? (slab_rows + 31) / 32 : 1;
   const int padded = slab_words + slab_words / 32 + 1;
   const size_t smem = (size_t)((padded + 3) / 4 * 4) * sizeof(uint32_t);

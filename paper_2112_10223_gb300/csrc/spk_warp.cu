@@ -26,6 +26,8 @@
 // When every segment has the same length L (Erdos-Renyi and partial-product
 // inputs), position e lies in segment umulhi(e, ceil(2^32/L)); full rounds run
 // without bounds checks.
+#include <type_traits>
+
 #include "spk_common.cuh"
 #include "spk_launch.h"
 
@@ -46,14 +48,13 @@ __host__ __device__ constexpr size_t warp_col_bytes(int smax) {
 }
 
 struct WarpColArgs {
-  const int32_t* list;     // warp-class column ids
+  const int32_t* list;     // warp-class global column ids
   const Counters* ctr;     // n_warp
   const int32_t* s_arr;    // s_j
   const int32_t* u_arr;    // numeric: u_j from the symbolic pass
-  const int64_t* col_ptr;  // numeric: B's column pointers
+  const int64_t* col_ptr;  // numeric: global column pointers of B
   int32_t* u_out;          // symbolic: u_j
-  int32_t* out_row;        // numeric: B row indices
-  void* out_val;           // numeric: B values
+  Outs out;                // numeric: where B goes
   Counters* ctr_w;
   int smax;
   int force_dedup;
@@ -132,76 +133,64 @@ __device__ __forceinline__ void for_each_entry(const ChunkMap& cm, const int32_t
   }
 }
 
-// All entries of column j: chunk by chunk of 32 inputs.  Resident mode
-// (k <= 32): the lane's input pointers and (beg, len) come from the caller.
+// All entries of local column j of the problem whose inputs are pointer-table
+// entries [off, off + k): chunk by chunk of 32 inputs.  Resident mode (a batch
+// of one with k <= 32): the lane's input pointers and (beg, len) come from
+// the caller.
 template <bool VALS, int U, typename V, typename F>
-__device__ __forceinline__ void for_each_column_entry(const Inputs& in, int j, bool resident, int rbeg, int rlen,
-                                                      const int32_t* my_ri, const V* my_va, int lane, F& f) {
+__device__ __forceinline__ void for_each_column_entry(const Inputs& in, int k, int off, int j, bool resident,
+                                                      int rbeg, int rlen, const int32_t* my_ri, const V* my_va,
+                                                      int lane, F& f) {
   if (resident) {
     ChunkMap cm;
-    cm.init(rbeg, rlen, lane, in.k);
+    cm.init(rbeg, rlen, lane, k);
     for_each_entry<VALS, U, V>(cm, my_ri + rbeg, VALS ? my_va + rbeg : my_va, lane, f);
     return;
   }
-  for (int cb = 0; cb < in.k; cb += 32) {
+  for (int cb = 0; cb < k; cb += 32) {
     const int i = cb + lane;
     int beg = 0, len = 0;
     const int32_t* ri = nullptr;
     const V* va = nullptr;
-    if (i < in.k) {
-      const int32_t* cp = in.cp[i];
+    if (i < k) {
+      const int32_t* cp = in.cp[off + i];
       beg = __ldg(cp + j);
       len = __ldg(cp + j + 1) - beg;
-      ri = in.ri[i] + beg;
-      if constexpr (VALS) va = static_cast<const V*>(in.val[i]) + beg;
+      ri = in.ri[off + i] + beg;
+      if constexpr (VALS) va = static_cast<const V*>(in.val[off + i]) + beg;
     }
     ChunkMap cm;
-    cm.init(beg, len, lane, min(32, in.k - cb));
+    cm.init(beg, len, lane, min(32, k - cb));
     for_each_entry<VALS, U, V>(cm, ri, va, lane, f);
   }
 }
 
-// Exclusive scan of n (a multiple of 32) padded counters; returns the total.
-__device__ __forceinline__ int warp_scan_pad(uint32_t* c, int n, int lane) {
-  const int per = n >> 5;
-  const int b0 = lane * per;
-  int loc = 0;
-  for (int t = 0; t < per; ++t) loc += (int)c[pad16(b0 + t)];
-  const int inc = warp_incl_scan(loc, lane);
-  int run = inc - loc;
-  for (int t = 0; t < per; ++t) {
-    const int p = pad16(b0 + t);
-    const int x = (int)c[p];
-    c[p] = (uint32_t)run;
-    run += x;
-  }
-  return __shfl_sync(SPK_FULL, inc, 31);
-}
-
 // Scalars of one warp-class column, loaded one column ahead of their use.
 struct ColState {
-  int j;    // column id, -1 past the end of the list
+  int g;    // global column id, -1 past the end of the list
+  int q;    // its problem
   int beg;  // resident mode: this lane's segment begin
   int len;  //                and length
   int s;    // sum of input lengths
   int u;    // numeric: distinct rows
-  int64_t out;
+  int64_t out;  // numeric: global col_ptr_B[g]
 };
 
-template <bool NUMERIC>
-__device__ __forceinline__ ColState load_col(const WarpColArgs& a, int cc, int ncols, bool resident,
-                                             const int32_t* my_cp, int lane, int k) {
-  ColState st{-1, 0, 0, 0, 0, 0};
+template <bool NUMERIC, bool BATCH>
+__device__ __forceinline__ ColState load_col(const Inputs& in, const WarpColArgs& a, int cc, int ncols,
+                                             bool resident, const int32_t* my_cp, int lane, int k0) {
+  ColState st{-1, 0, 0, 0, 0, 0, 0};
   if (cc >= ncols) return st;
-  st.j = a.list[cc];
-  st.s = a.s_arr[st.j];
+  st.g = a.list[cc];
+  if (BATCH) st.q = __ldg(in.col_inst + st.g);
+  st.s = a.s_arr[st.g];
   if (NUMERIC) {
-    st.u = a.u_arr[st.j];
-    st.out = a.col_ptr[st.j];
+    st.u = a.u_arr[st.g];
+    st.out = a.col_ptr[st.g];
   }
-  if (resident && lane < k) {
-    st.beg = __ldg(my_cp + st.j);
-    st.len = __ldg(my_cp + st.j + 1) - st.beg;
+  if (resident && lane < k0) {
+    st.beg = __ldg(my_cp + st.g);
+    st.len = __ldg(my_cp + st.g + 1) - st.beg;
   }
   return st;
 }
@@ -230,149 +219,193 @@ struct BucketFile {  // pass 2: file the row (and value) at the bucket's next sl
   }
 };
 
-template <typename V, bool NUMERIC, int WARPS, int U>
-__global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColArgs a) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ uint32_t s_mul[16];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x < 16) {
-    const uint64_t nb = 1ull << threadIdx.x;
-    s_mul[threadIdx.x] = nb >= (uint64_t)in.m ? 0xFFFFFFFFu : (uint32_t)((nb << 32) / (uint64_t)in.m);
+// Per-warp shared buffers.
+struct WarpSmem {
+  unsigned char* vals;  // numeric values (room for smax doubles in a mixed batch)
+  int32_t* skey;
+  uint32_t* cnt;
+  uint32_t* mlist;      // (start | size << 16) of multi-entry buckets
+};
+
+// One column: the three passes, the bucket sorts and (numeric) the write of
+// B(:,j).  Symbolic returns the number of repeated rows; numeric returns 0.
+template <typename V, bool NUMERIC, int U>
+__device__ __forceinline__ int warp_column(const Inputs& in, const WarpColArgs& a, const WarpSmem& sm,
+                                           const ColState& cur, int k, int off, int j, uint32_t mul, int NB,
+                                           int32_t* out_row, void* out_val_raw, bool resident,
+                                           const int32_t* my_ri, const void* my_va_raw, int lane) {
+  const int s = cur.s;
+  V* sval = reinterpret_cast<V*>(sm.vals);
+  int32_t* skey = sm.skey;
+  uint32_t* cnt = sm.cnt;
+  uint32_t* mlist = sm.mlist;
+  const V* my_va = static_cast<const V*>(my_va_raw);
+  for (int b = lane; b < padded_words(NB); b += 32) cnt[b] = 0u;
+  __syncwarp();
+  // Pass 1: entries per bucket.
+  BucketCount<V> count{cnt, mul};
+  for_each_column_entry<false, U, V>(in, k, off, j, resident, cur.beg, cur.len, my_ri, my_va, lane, count);
+  __syncwarp();
+  // Scan the counts into bucket starts; list the buckets with two or more
+  // entries on the way (they are the only ones that need sorting).
+  int nmulti = 0;
+  {
+    const int per = NB >> 5;
+    const int b0 = lane * per;
+    int loc = 0;
+    for (int t = 0; t < per; ++t) loc += (int)cnt[pad16(b0 + t)];
+    const int inc = warp_incl_scan(loc, lane);
+    int run = inc - loc;
+    for (int t = 0; t < per; ++t) {
+      const int p = pad16(b0 + t);
+      const int x = (int)cnt[p];
+      cnt[p] = (uint32_t)run;
+      const bool multi = x >= 2;
+      const unsigned bal = __ballot_sync(SPK_FULL, multi);
+      if (multi) mlist[nmulti + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)run | ((uint32_t)x << 16);
+      nmulti += __popc(bal);
+      run += x;
+    }
   }
-  __syncthreads();
+  __syncwarp();
+  // Pass 2: file every entry at its bucket's next slot.
+  BucketFile<V, NUMERIC> file{cnt, skey, sval, mul};
+  for_each_column_entry<NUMERIC, U, V>(in, k, off, j, resident, cur.beg, cur.len, my_ri, my_va, lane, file);
+  __syncwarp();
+  // Sort the multi-entry buckets, one bucket per lane (insertion sort; they
+  // hold 2-3 entries mostly).  Symbolic: count the repeated rows met.
+  int dups = 0;
+  for (int i = lane; i < nmulti; i += 32) {
+    const uint32_t w = mlist[i];
+    const int lo = (int)(w & 0xffffu), hi = lo + (int)(w >> 16);
+    for (int x = lo + 1; x < hi; ++x) {
+      const int32_t kx = skey[x];
+      V vx;
+      if constexpr (NUMERIC) vx = sval[x];
+      int y = x - 1;
+      while (y >= lo && skey[y] > kx) {
+        skey[y + 1] = skey[y];
+        if constexpr (NUMERIC) sval[y + 1] = sval[y];
+        --y;
+      }
+      skey[y + 1] = kx;
+      if constexpr (NUMERIC) sval[y + 1] = vx;
+    }
+    if constexpr (!NUMERIC)
+      for (int x = lo + 1; x < hi; ++x) dups += skey[x] == skey[x - 1];
+  }
+  __syncwarp();
+  if constexpr (!NUMERIC) return warp_sum(dups);
+  // The s slots now hold the column's entries sorted by row.  A row's first
+  // slot is its leader; leaders before slot q = ballot prefix.
+  if constexpr (NUMERIC) {
+    const int u = cur.u;
+    V* out_val = static_cast<V*>(out_val_raw);
+    if (!a.force_dedup && u == s) {
+      for (int q = lane; q < s; q += 32) {  // no repeated row: copy out
+        out_row[q] = skey[q];
+        out_val[q] = sval[q];
+      }
+    } else {
+      int before = 0;
+      int32_t carry = -1;  // last row of the previous 32 slots
+      for (int q0 = 0; q0 < s; q0 += 32) {
+        const int q = q0 + lane;
+        const int32_t key = q < s ? skey[q] : -2;
+        int32_t prev = __shfl_up_sync(SPK_FULL, key, 1);
+        if (lane == 0) prev = carry;
+        const bool lead = q < s && key != prev;
+        const unsigned bal = __ballot_sync(SPK_FULL, lead);
+        if (lead) {
+          V sum = sval[q];
+          for (int y = q + 1; y < s && skey[y] == key; ++y) sum += sval[y];
+          const int pos = before + __popc(bal & ((1u << lane) - 1u));
+          if (pos < u) {
+            out_row[pos] = key;
+            out_val[pos] = sum;
+          }
+        }
+        before += __popc(bal);
+        carry = __shfl_sync(SPK_FULL, key, 31);
+      }
+      if (before != u && lane == 0) atomicOr(&a.ctr_w->err, ERR_INTERNAL);  // symbolic and numeric disagree
+    }
+    return 0;
+  }
+}
+
+// DT: 0 = every problem float, 1 = every problem double, 2 = per-problem
+// dtype (a mixed batch; shared memory sized for doubles).  BATCH: columns of
+// several problems (looked up per column); otherwise one problem, whose
+// inputs' pointers lanes may hold for the whole launch (resident mode).
+template <int DT, bool NUMERIC, bool BATCH, int WARPS, int U>
+__global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColArgs a) {
+  using VB = typename std::conditional<DT == 0, float, double>::type;  // value bytes per slot
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int smax = a.smax;
-  unsigned char* base = sm_raw + (size_t)wid * warp_col_bytes<V, NUMERIC>(smax);
-  V* sval = reinterpret_cast<V*>(base);  // numeric only
-  int32_t* skey = reinterpret_cast<int32_t*>(base + (NUMERIC ? (size_t)smax * sizeof(V) : 0));
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(skey + smax);
-  uint32_t* mlist = cnt + padded_words(smax);  // (start | size << 16) of multi-entry buckets
+  unsigned char* base = sm_raw + (size_t)wid * warp_col_bytes<VB, NUMERIC>(smax);
+  WarpSmem sm;
+  sm.vals = base;
+  sm.skey = reinterpret_cast<int32_t*>(base + (NUMERIC ? (size_t)smax * sizeof(VB) : 0));
+  sm.cnt = reinterpret_cast<uint32_t*>(sm.skey + smax);
+  sm.mlist = sm.cnt + padded_words(smax);
+  __shared__ uint32_t s_mul[16];
+  if (!BATCH && threadIdx.x < 16) s_mul[threadIdx.x] = in.inst[0].bucket_mul[threadIdx.x];
+  __syncthreads();
   const int ncols = a.ctr->n_warp;
-  const bool resident = in.k <= 32;
+  const int k0 = in.inst[0].k;
+  const bool resident = !BATCH && k0 <= 32;
   const int32_t* my_cp = nullptr;
   const int32_t* my_ri = nullptr;
-  const V* my_va = nullptr;
-  if (resident && lane < in.k) {
+  const void* my_va = nullptr;
+  if (resident && lane < k0) {
     my_cp = in.cp[lane];
     my_ri = in.ri[lane];
-    if constexpr (NUMERIC) my_va = static_cast<const V*>(in.val[lane]);
+    if constexpr (NUMERIC) my_va = in.val[lane];
   }
-  int32_t* out_row = a.out_row;
-  V* out_val = static_cast<V*>(a.out_val);
   const int stride = gridDim.x * WARPS;
   int c = blockIdx.x * WARPS + wid;
   // Scalars of the current column and of the next one (loaded a column ahead).
-  ColState cur = load_col<NUMERIC>(a, c, ncols, resident, my_cp, lane, in.k);
-  ColState nxt = load_col<NUMERIC>(a, c + stride, ncols, resident, my_cp, lane, in.k);
+  ColState cur = load_col<NUMERIC, BATCH>(in, a, c, ncols, resident, my_cp, lane, k0);
+  ColState nxt = load_col<NUMERIC, BATCH>(in, a, c + stride, ncols, resident, my_cp, lane, k0);
   int n_unique = 0;
-  while (cur.j >= 0) {
-    const int j = cur.j, beg = cur.beg, len = cur.len, s = cur.s, u = cur.u;
-    const int64_t out = cur.out;
-    const int qb = max(5, ceil_log2(s));
+  while (cur.g >= 0) {
+    // One problem: its scalars were hoisted; a batch looks them up per column.
+    const Inst* I = in.inst + cur.q;
+    const int k = BATCH ? I->k : k0;
+    const int off = BATCH ? I->ptr_off : 0;
+    const int j = BATCH ? cur.g - I->colbase : cur.g;
+    const int qb = max(5, ceil_log2(cur.s));
     const int NB = 1 << qb;
     if (NB > smax) {  // not reachable for a warp-class column
       if (lane == 0) atomicOr(&a.ctr_w->err, ERR_INTERNAL);
     } else {
-      const uint32_t mul = s_mul[qb];
-      for (int b = lane; b < padded_words(NB); b += 32) cnt[b] = 0u;
-      __syncwarp();
-      // Pass 1: entries per bucket.
-      BucketCount<V> count{cnt, mul};
-      for_each_column_entry<false, U, V>(in, j, resident, beg, len, my_ri, my_va, lane, count);
-      __syncwarp();
-      // Scan the counts into bucket starts; list the buckets with two or more
-      // entries on the way (they are the only ones that need sorting).
-      int nmulti = 0;
-      {
-        const int per = NB >> 5;
-        const int b0 = lane * per;
-        int loc = 0;
-        for (int t = 0; t < per; ++t) loc += (int)cnt[pad16(b0 + t)];
-        const int inc = warp_incl_scan(loc, lane);
-        int run = inc - loc;
-        for (int t = 0; t < per; ++t) {
-          const int p = pad16(b0 + t);
-          const int x = (int)cnt[p];
-          cnt[p] = (uint32_t)run;
-          const bool multi = x >= 2;
-          const unsigned bal = __ballot_sync(SPK_FULL, multi);
-          if (multi) mlist[nmulti + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)run | ((uint32_t)x << 16);
-          nmulti += __popc(bal);
-          run += x;
-        }
-      }
-      __syncwarp();
-      // Pass 2: file every entry at its bucket's next slot.
-      BucketFile<V, NUMERIC> file{cnt, skey, sval, mul};
-      for_each_column_entry<NUMERIC, U, V>(in, j, resident, beg, len, my_ri, my_va, lane, file);
-      __syncwarp();
-      // Sort the multi-entry buckets, one bucket per lane (insertion sort; they
-      // hold 2-3 entries mostly).  Symbolic: count the repeated rows met.
-      int dups = 0;
-      for (int i = lane; i < nmulti; i += 32) {
-        const uint32_t w = mlist[i];
-        const int lo = (int)(w & 0xffffu), hi = lo + (int)(w >> 16);
-        for (int x = lo + 1; x < hi; ++x) {
-          const int32_t kx = skey[x];
-          V vx;
-          if constexpr (NUMERIC) vx = sval[x];
-          int y = x - 1;
-          while (y >= lo && skey[y] > kx) {
-            skey[y + 1] = skey[y];
-            if constexpr (NUMERIC) sval[y + 1] = sval[y];
-            --y;
-          }
-          skey[y + 1] = kx;
-          if constexpr (NUMERIC) sval[y + 1] = vx;
-        }
-        if constexpr (!NUMERIC)
-          for (int x = lo + 1; x < hi; ++x) dups += skey[x] == skey[x - 1];
-      }
-      __syncwarp();
+      const uint32_t mul = BATCH ? __ldg(&I->bucket_mul[qb]) : s_mul[qb];
       if constexpr (!NUMERIC) {
-        dups = warp_sum(dups);
+        const int dups = warp_column<int32_t, false, U>(in, a, sm, cur, k, off, j, mul, NB, nullptr, nullptr,
+                                                        resident, my_ri, my_va, lane);
         if (lane == 0) {
-          a.u_out[j] = s - dups;
+          a.u_out[cur.g] = cur.s - dups;
           n_unique += (dups == 0);
         }
-      }
-      // The s slots now hold the column's entries sorted by row.  A row's
-      // first slot is its leader; leaders before slot q = ballot prefix.
-      if constexpr (NUMERIC) {
-        if (!a.force_dedup && u == s) {
-          for (int q = lane; q < s; q += 32) {  // no repeated row: copy out
-            out_row[out + q] = skey[q];
-            out_val[out + q] = sval[q];
-          }
-        } else {
-          int before = 0;
-          int32_t carry = -1;  // last row of the previous 32 slots
-          for (int q0 = 0; q0 < s; q0 += 32) {
-            const int q = q0 + lane;
-            const int32_t key = q < s ? skey[q] : -2;
-            int32_t prev = __shfl_up_sync(SPK_FULL, key, 1);
-            if (lane == 0) prev = carry;
-            const bool lead = q < s && key != prev;
-            const unsigned bal = __ballot_sync(SPK_FULL, lead);
-            if (lead) {
-              V sum = sval[q];
-              for (int y = q + 1; y < s && skey[y] == key; ++y) sum += sval[y];
-              const int pos = before + __popc(bal & ((1u << lane) - 1u));
-              if (pos < u) {
-                out_row[out + pos] = key;
-                out_val[out + pos] = sum;
-              }
-            }
-            before += __popc(bal);
-            carry = __shfl_sync(SPK_FULL, key, 31);
-          }
-          if (before != u && lane == 0) atomicOr(&a.ctr_w->err, ERR_INTERNAL);  // symbolic and numeric disagree
-        }
+      } else {
+        // B(:,j) starts at col_ptr_B[g] - col_ptr_B[colbase] in its problem's buffers.
+        const int64_t out = cur.out - (BATCH ? a.col_ptr[I->colbase] : 0);
+        int32_t* orow = (BATCH ? out_row_of(a.out, cur.q) : a.out.row0) + out;
+        void* oval = BATCH ? out_val_of(a.out, cur.q) : a.out.val0;
+        if (DT == 1 || (DT == 2 && I->dtype == 1))
+          warp_column<double, true, U>(in, a, sm, cur, k, off, j, mul, NB, orow, static_cast<double*>(oval) + out,
+                                       resident, my_ri, my_va, lane);
+        else
+          warp_column<float, true, U>(in, a, sm, cur, k, off, j, mul, NB, orow, static_cast<float*>(oval) + out,
+                                      resident, my_ri, my_va, lane);
       }
     }
     __syncwarp();
     c += stride;
     cur = nxt;
-    nxt = load_col<NUMERIC>(a, c + stride, ncols, resident, my_cp, lane, in.k);
+    nxt = load_col<NUMERIC, BATCH>(in, a, c + stride, ncols, resident, my_cp, lane, k0);
   }
   if (!NUMERIC && lane == 0 && n_unique) atomicAdd(&a.ctr_w->n_unique, n_unique);
 }
@@ -395,13 +428,16 @@ static int blocks_per_sm(const DeviceInfo& dev, size_t smem_per_block, int threa
   return b < 1 ? 1 : b;
 }
 
-template <typename V, bool NUMERIC>
+template <int DT, bool NUMERIC>
 static cudaError_t launch_warp_col(const Inputs& in, WarpColArgs a, int warp_max, int n_cols_hint,
                                    const DeviceInfo& dev, cudaStream_t st) {
+  using VB = typename std::conditional<DT == 0, float, double>::type;
   constexpr int WARPS = 8;
   a.smax = pow2_at_least(warp_max) < 32 ? 32 : pow2_at_least(warp_max);
-  const size_t smem = (size_t)WARPS * warp_col_bytes<V, NUMERIC>(a.smax);
-  auto kern = k_warp_col<V, NUMERIC, WARPS, NUMERIC ? 8 : 16>;
+  const size_t smem = (size_t)WARPS * warp_col_bytes<VB, NUMERIC>(a.smax);
+  // A mixed-dtype launch is always a batch.
+  auto kern = (DT == 2 || in.col_inst) ? k_warp_col<DT, NUMERIC, true, WARPS, NUMERIC ? 8 : 16>
+                                       : k_warp_col<DT == 2 ? 1 : DT, NUMERIC, false, WARPS, NUMERIC ? 8 : 16>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = dev.sms * blocks_per_sm(dev, smem + 128, WARPS * 32);
@@ -422,12 +458,12 @@ cudaError_t launch_sym_warp(const Inputs& in, const int32_t* list, const int32_t
   a.s_arr = s;
   a.u_out = u;
   a.ctr_w = ctr_w;
-  return launch_warp_col<int32_t, false>(in, a, warp_max, -1, dev, st);
+  return launch_warp_col<0, false>(in, a, warp_max, -1, dev, st);
 }
 
-cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, const Counters* ctr, int n_cols,
-                            const int32_t* s, const int32_t* u, const int64_t* col_ptr, int32_t* out_row,
-                            void* out_val, int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev,
+cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const Counters* ctr, int n_cols,
+                            const int32_t* s, const int32_t* u, const int64_t* col_ptr, const Outs& out,
+                            int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev,
                             cudaStream_t st) {
   if (n_cols <= 0) return cudaSuccess;
   WarpColArgs a{};
@@ -436,12 +472,12 @@ cudaError_t launch_num_warp(const Inputs& in, bool f64, const int32_t* list, con
   a.s_arr = s;
   a.u_arr = u;
   a.col_ptr = col_ptr;
-  a.out_row = out_row;
-  a.out_val = out_val;
+  a.out = out;
   a.ctr_w = ctr_w;
   a.force_dedup = force_dedup;
-  return f64 ? launch_warp_col<double, true>(in, a, warp_max, n_cols, dev, st)
-             : launch_warp_col<float, true>(in, a, warp_max, n_cols, dev, st);
+  if (dt == 0) return launch_warp_col<0, true>(in, a, warp_max, n_cols, dev, st);
+  if (dt == 1) return launch_warp_col<1, true>(in, a, warp_max, n_cols, dev, st);
+  return launch_warp_col<2, true>(in, a, warp_max, n_cols, dev, st);
 }
 
 }  // namespace spk

@@ -32,7 +32,8 @@ import math
 
 import torch
 
-__all__ = ["er", "rmat", "spgemm_like", "random_csc", "values", "to_device", "batch_instance_params", "take_columns"]
+__all__ = ["er", "rmat", "spgemm_like", "random_csc", "values", "to_device", "batch_instance_params", "take_columns",
+           "instance", "instance_nnz_estimate"]
 
 
 def _gen(seed: int, device) -> torch.Generator:
@@ -257,3 +258,103 @@ def take_columns(A, cols: torch.Tensor):
             idx = torch.zeros(0, dtype=torch.int64, device=cp.device)
         out.append((sub_cp.to(torch.int32), ri[idx], va[idx]))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Batch instances: every column j of an instance has one length L_j, shared by
+# the instance's k inputs (so the inputs share one col_ptr array).
+# ---------------------------------------------------------------------------
+def _distinct_rows_var(g, L: torch.Tensor, m: int, reps: int, device, max_elems: int = 1 << 26) -> torch.Tensor:
+    """(reps, sum(L)) int32: for every rep and column j, L_j distinct uniform rows of [0, m), ascending.
+
+    Draw L_j uniform rows; while a value repeats, redraw the repeats.  The
+    result is the set of the first L_j distinct values of an iid uniform
+    sequence, i.e. a uniform L_j-subset of [0, m).  Columns with L_j = m take
+    every row.
+    """
+    n = L.numel()
+    total = int(L.sum())
+    out = torch.empty((reps, total), dtype=torch.int32, device=device)
+    if n == 0 or total == 0 or reps == 0:
+        return out
+    Lmax = int(L.max())
+    if Lmax > m:
+        raise ValueError("L_j > m")
+    valid = torch.arange(Lmax, device=device)[None, :] < L[:, None]  # (n, Lmax)
+    full = (L == m)[None, :, None]
+    every = torch.arange(Lmax, device=device, dtype=torch.int64)[None, None, :]
+    chunk = max(1, max_elems // (n * Lmax))
+    for r0 in range(0, reps, chunk):
+        c = min(chunk, reps - r0)
+        x = torch.randint(0, m, (c, n, Lmax), generator=g, device=device, dtype=torch.int64)
+        x = torch.where(full, every, x)
+        x = torch.where(valid[None], x, m).sort(dim=-1).values
+        bad = ((x[..., 1:] == x[..., :-1]) & valid[None, :, 1:]).any(dim=-1).nonzero()  # (nb, 2)
+        while bad.shape[0]:
+            y = x[bad[:, 0], bad[:, 1]]  # (nb, Lmax), sorted, padding m at the end
+            rep = torch.zeros_like(y, dtype=torch.bool)
+            rep[:, 1:] = y[:, 1:] == y[:, :-1]
+            rep &= y < m
+            fresh = torch.randint(0, m, y.shape, generator=g, device=device, dtype=torch.int64)
+            y = torch.where(rep, fresh, y).sort(dim=-1).values
+            x[bad[:, 0], bad[:, 1]] = y
+            still = ((y[:, 1:] == y[:, :-1]) & (y[:, 1:] < m)).any(dim=-1)
+            bad = bad[still]
+        out[r0:r0 + c] = x[:, valid].to(torch.int32)
+    return out
+
+
+def instance(params: dict, device="cpu"):
+    """The inputs of one batch instance drawn by batch_instance_params.
+
+    Returns (A, m): A is a list of k CSC tuples sharing one col_ptr.  Column
+    lengths L_j are uniform on params["L_range"] (inclusive).  "er": every
+    input draws L_j distinct uniform rows of column j.  "spgemm_like": column
+    j has a candidate set of min(4 L_j, m) distinct uniform rows and every
+    input draws L_j distinct rows of it (partial products of an SpGEMM).
+    Values are uniform on [-1, 1] on the exact grid of ``values``.
+    """
+    g = _gen(params["seed"], device)
+    k, m = params["k"], params["m"]
+    n = params.get("n", m)
+    dtype = params["dtype"]
+    lo, hi = params["L_range"]
+    L = torch.randint(lo, hi + 1, (n,), generator=g, device=device, dtype=torch.int64)
+    L = torch.clamp(L, max=m)
+    col_ptr64 = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    col_ptr64[1:] = torch.cumsum(L, 0)
+    tot = int(col_ptr64[-1])
+    if tot >= 2 ** 31:
+        raise ValueError("instance input too large for int32 col_ptr")
+    col_ptr = col_ptr64.to(torch.int32)
+    if params["family"] == "er":
+        rows = _distinct_rows_var(g, L, m, k, device)
+    else:
+        C = torch.clamp(4 * L, max=m)
+        cand = _distinct_rows_var(g, C, m, 1, device)[0]  # (sum C,)
+        Cmax = int(C.max())
+        cptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+        cptr[1:] = torch.cumsum(C, 0)
+        cvalid = torch.arange(Cmax, device=device)[None, :] < C[:, None]
+        cand_pad = torch.zeros((n, Cmax), dtype=torch.int32, device=device)
+        cand_pad[cvalid] = cand
+        Lmax = int(L.max())
+        lvalid = torch.arange(Lmax, device=device)[None, :] < L[:, None]
+        rows = torch.empty((k, tot), dtype=torch.int32, device=device)
+        chunk = max(1, (1 << 26) // (n * Cmax))
+        for i0 in range(0, k, chunk):
+            c = min(chunk, k - i0)
+            key = torch.rand((c, n, Cmax), generator=g, device=device)
+            key = torch.where(cvalid[None], key, 2.0)
+            pos = key.argsort(dim=-1)[..., :Lmax]
+            pos = torch.where(lvalid[None], pos, Cmax).sort(dim=-1).values.clamp_(max=Cmax - 1)
+            picked = torch.gather(cand_pad[None].expand(c, n, Cmax), 2, pos)
+            rows[i0:i0 + c] = picked[:, lvalid]
+    vals = values(g, k * tot, dtype, "uniform", device).reshape(k, tot)
+    return [(col_ptr, rows[i], vals[i]) for i in range(k)], m
+
+
+def instance_nnz_estimate(params: dict) -> int:
+    """Expected input nnz of an instance (k * n * mean L), for memory planning."""
+    lo, hi = params["L_range"]
+    return int(params["k"] * params.get("n", params["m"]) * min((lo + hi) / 2.0, params["m"]))

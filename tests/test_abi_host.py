@@ -143,3 +143,55 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(spk, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(spk.SpkaddError):
         spk.library()
+
+
+def _batch_plan(lib, problems, dtypes=None, count=None):
+    """problems: list of lists of CSC; returns (status, handle)."""
+    arrs = [(spk.CSC * len(p))(*p) for p in problems]
+    ks = (ctypes.c_int * max(1, len(problems)))(*[len(p) for p in problems])
+    ptrs = (ctypes.c_void_p * max(1, len(problems)))(*[ctypes.cast(a, ctypes.c_void_p) for a in arrs])
+    dts = (ctypes.c_int * max(1, len(problems)))(*(dtypes or [1] * len(problems)))
+    h = ctypes.c_void_p(123)
+    st = lib.spkadd_batch_plan(ctypes.byref(h), len(problems) if count is None else count,
+                               ctypes.cast(ks, ctypes.c_void_p), ctypes.cast(ptrs, ctypes.c_void_p),
+                               ctypes.cast(dts, ctypes.c_void_p), None, None)
+    return st, h
+
+
+@pytest.mark.parametrize("case,expect", [
+    ("count0", 1), ("k0", 1), ("shape_inside_problem", 2), ("bad_dtype", 1), ("second_problem_overflow", 5),
+    ("total_columns_overflow", 5),
+])
+def test_batch_plan_rejects_bad_arguments_without_cuda(lib, case, expect):
+    # Problems may differ in shape from each other; inside one they may not.
+    problems = [[_csc(m=4, n=3), _csc(m=4, n=3)], [_csc(m=9, n=5)]]
+    dtypes, count = [1, 0], None
+    if case == "count0":
+        count = 0
+    elif case == "k0":
+        problems[1] = []
+    elif case == "shape_inside_problem":
+        problems[0][1].n = 4
+    elif case == "bad_dtype":
+        dtypes = [1, 3]
+    elif case == "second_problem_overflow":
+        problems[1][0].nnz = 2 ** 31
+    elif case == "total_columns_overflow":
+        problems[0][0].n = problems[0][1].n = 2 ** 30
+        problems[1][0].n = 2 ** 30
+    st, h = _batch_plan(lib, problems, dtypes=dtypes, count=count)
+    assert st == expect, spk.spkadd_status_string(st)
+    assert not h.value
+
+
+def test_batch_calls_on_null_handle(lib):
+    n = (ctypes.c_int64 * 1)()
+    assert lib.spkadd_batch_symbolic(None, ctypes.cast(n, ctypes.c_void_p)) == 1
+    assert lib.spkadd_batch_numeric(None, None, None, None) == 1
+
+
+def test_batch_descriptor_layout_matches_the_header():
+    # The binding packs descriptors with numpy; the record must be spkadd_csc.
+    assert spk._CSC_NP.itemsize == ctypes.sizeof(spk.CSC) == 48
+    assert [spk._CSC_NP.fields[f][1] for f in ("m", "n", "nnz", "col_ptr", "row_idx", "val")] == \
+        [getattr(spk.CSC, f).offset for f in ("m", "n", "nnz", "col_ptr", "row_idx", "val")]
