@@ -206,7 +206,7 @@ static spkadd_status check_problem(int k, const spkadd_csc* A, spkadd_dtype dtyp
 }
 
 // Numeric work items one problem can produce: heavy windows <= nnz /
-// (window_max - 32) + one per heavy column and slab; CTA columns <=
+// (window_max - 64) + one per heavy column and slab; CTA columns <=
 // min(n, nnz / (warp_max + 1)).
 static int64_t window_bound(int64_t m, int64_t n, int64_t nnz, const spkadd_options& o) {
   const int64_t slab_rows = (int64_t)1 << spk::SLAB_BITS;
@@ -215,7 +215,7 @@ static int64_t window_bound(int64_t m, int64_t n, int64_t nnz, const spkadd_opti
   if (heavy_cols > n) heavy_cols = n;
   int64_t cta_cols = nnz / (o.warp_max + 1);
   if (cta_cols > n) cta_cols = n;
-  return nnz / (o.window_max - 32) + heavy_cols * (slabs + 1) + cta_cols + 16;
+  return nnz / (o.window_max - 64) + heavy_cols * (slabs + 1) + cta_cols + 16;
 }
 
 // Plans `count` problems (count = 1 and batch = false for spkadd_plan).

@@ -283,6 +283,15 @@ __device__ __forceinline__ uint32_t bucket_hi(int32_t r, uint32_t mul) {
   return __umulhi(static_cast<uint32_t>(r), mul);
 }
 
+// Sets bit rr of a 64-bit-word bitmap with a 32-bit atomic on the word's
+// half that holds it.  Returns true when that half was empty before (then the
+// 64-bit word may have been empty: the caller marks it in its summary; a
+// word can be marked twice, which is harmless).
+__device__ __forceinline__ bool set_row_bit(unsigned long long* bm, uint32_t rr) {
+  uint32_t* half = reinterpret_cast<uint32_t*>(bm) + (rr >> 5);  // little-endian: bits 0-31 first
+  return atomicOr(half, 1u << (rr & 31)) == 0u;
+}
+
 // Warp-wide exclusive scan of n 32-bit counters (n a multiple of 32) in place;
 // returns the total.
 __device__ __forceinline__ int warp_scan32(uint32_t* c, int n, int lane) {

@@ -1,18 +1,28 @@
-// spk_numeric.cu -- a4/a5 of the hot path: accumulate values and write each
-// output column sorted by row.
+// spk_numeric.cu -- a4/a5 of the hot path for thread-block work items: the
+// CTA-class columns and the row windows of heavy columns.  Accumulate the
+// values and write each item's output rows sorted.
 //
-// Accumulation is Alg. 5 (HashAdd): an open-addressing table in shared memory
-// holding (row, value) pairs, empty = -1, linear probing, insert-or-add.  The
-// row key is claimed with atomicCAS and the value added with a shared-memory
-// atomicAdd, so the lanes of a warp insert concurrently.  Table size is a power
-// of two >= 2 nnz(B(:,j)) (from the symbolic pass).
+// Alg. 5 (HashAdd) keeps an insert-or-add table keyed by row and sorts it at
+// the end; Sec. II-D allows a dense accumulator in place of the hash.  Here the
+// table is indexed by the exact output rank of the row, taken from a bitmap of
+// the item's rows (the symbolic pass's structure, rebuilt in shared memory):
 //
-// Thread-block items (CTA-class columns and heavy-column windows) use that
-// open-addressing table with the scrambled hash, then sort (the last step of
-// Alg. 5): occupied slots are compacted, bucketed by an order-preserving map
-// of the row onto [rmin, rmax], placed by a counting sort and ranked inside
-// their bucket.  Warp-class columns use a bucketed, order-preserving hash
-// instead (spk_warp.cu), which makes the sort step a counting placement.
+//   pass A   every entry sets bit (r - lo) of a 64-bit-word row bitmap; the
+//            first bit set in a word also sets the word's bit in a summary
+//            bitmap (one bit per word)
+//   rank     the non-empty words (found through the summary) get the
+//            exclusive popcount prefix of the words before them, and are
+//            listed in row order
+//   pass B   every entry adds its value at acc[rank(r)], rank(r) =
+//            prefix(word) + popcount(word & bits below r)
+//   write    the listed words are expanded to rows in rank order (one thread
+//            per word) and rows and acc[rank] are written out coalesced,
+//            already in row order; the touched words are cleared for the next
+//            item.
+//
+// The bitmap covers a slab of 2^slab_log2 rows (at most 2^20): an item whose
+// rows span more is processed slab by slab, with per-input binary searches
+// for each slab's entries.
 #include <type_traits>
 
 #include "spk_common.cuh"
@@ -20,212 +30,241 @@
 
 namespace spk {
 
-// Padded layouts of the thread-block kernel: table slot p lives at sp(p) (one
-// pad slot per 32) and counter word w at cw(w) (one pad word per 4), so a
-// thread that walks a contiguous run of slots or words starts on its own bank.
-__device__ __forceinline__ int sp(int p) { return p + (p >> 5); }
-__host__ __device__ __forceinline__ int cw(int w) { return w + (w >> 2); }
-__device__ __forceinline__ uint32_t get16p(const uint32_t* c, uint32_t h) {
-  return (c[cw((int)(h >> 1))] >> ((h & 1u) << 4)) & 0xffffu;
+constexpr int NUM_SLAB_LOG2_MAX = 20;  // 2^20 rows: 128 KB of bitmap
+
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(SPK_FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
 }
-__device__ __forceinline__ uint32_t add16p(uint32_t* c, uint32_t h) {
-  const uint32_t sh = (h & 1u) << 4;
-  return (atomicAdd(&c[cw((int)(h >> 1))], 1u << sh) >> sh) & 0xffffu;
-}
+
+// Block-wide exclusive scan of one 64-bit value per thread; `tmp` holds
+// BLOCK/32 + 1 entries.  Contains __syncthreads().
 template <int BLOCK>
-__device__ __forceinline__ void block_scan16p(uint32_t* c, int n, int* red) {
-  const int nw = n >> 1;
-  const int per = (nw + BLOCK - 1) / BLOCK;
-  const int w0 = threadIdx.x * per;
-  int loc = 0;
-  for (int t = 0; t < per; ++t)
-    if (w0 + t < nw) {
-      const uint32_t x = c[cw(w0 + t)];
-      loc += (int)(x & 0xffffu) + (int)(x >> 16);
-    }
-  int total;
-  int run = block_excl_scan<BLOCK>(loc, red, &total);
-  for (int t = 0; t < per; ++t)
-    if (w0 + t < nw) {
-      const uint32_t x = c[cw(w0 + t)];
-      const int lo = (int)(x & 0xffffu), hi = (int)(x >> 16);
-      c[cw(w0 + t)] = (uint32_t)run | ((uint32_t)(run + lo) << 16);
-      run += lo + hi;
-    }
-}
-
-// Order-preserving bucket of row r on [rmin, rmin + span): floor((r-rmin)*NB/span).
-__device__ __forceinline__ uint32_t bucket_of(int32_t r, int32_t rmin, uint64_t bmul) {
-  return (uint32_t)(((uint64_t)(uint32_t)(r - rmin) * bmul) >> 32);
-}
-
-// Insert-or-add with the padded slot layout (slot h at sp(h)).
-__device__ __forceinline__ int table_insert_pad(int32_t* keys, uint32_t h, uint32_t mask, int32_t r, bool& fresh) {
-  fresh = false;
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    const int old = atomicCAS(&keys[sp((int)h)], -1, r);
-    if (old == -1) {
-      fresh = true;
-      return (int)h;
-    }
-    if (old == r) return (int)h;
-    h = (h + 1) & mask;
-  }
-  return -1;
-}
-
-// One thread-block work item: a CTA-class column or a heavy column's row
-// window (Alg. 8: B(r1:r2, j) <- HashAdd(A_1(r1:r2, j), ..., A_k(r1:r2, j))).
-// `sm_raw` holds the table (values sized for V), then the row keys, then the
-// padded 16-bit bucket counters.
-template <typename V, int BLOCK, int U, int SMAX>
-__device__ __forceinline__ void cta_item(const Inputs& in, const Window& W, const Inst* I, const int32_t* offs,
-                                         int32_t* __restrict__ out_row, V* __restrict__ out_val,
-                                         unsigned char* sm_raw, int tmax, int* red, int* s_rng, Counters* ctr_w) {
-  constexpr int NW = BLOCK / 32;
+__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long x, unsigned long long* tmp,
+                                                                  unsigned long long* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  V* vals = reinterpret_cast<V*>(sm_raw);
-  int32_t* keys = reinterpret_cast<int32_t*>(vals + sp(tmax));
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(keys + sp(tmax));  // tmax/2 16-bit counters, padded
-  const int u = W.u;
-  const int k = I->k, off = I->ptr_off, j = W.col - I->colbase;
-  const int q = max(7, ceil_log2(2 * u));  // >= 64 counters: enough buckets for any span at M = 1
-  const int T = 1 << q;
-  if (T > tmax || T / BLOCK > SMAX) {
-    if (threadIdx.x == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
-    return;
-  }
-  const uint32_t mask = (uint32_t)T - 1u;
-  for (int p = threadIdx.x; p < T; p += BLOCK) {
-    keys[sp(p)] = -1;
-    vals[sp(p)] = V(0);
-  }
-  for (int p = threadIdx.x; p < cw(T / 4); p += BLOCK) cnt[p] = 0u;
-  if (threadIdx.x == 0) {
-    s_rng[0] = INT32_MAX;
-    s_rng[1] = -1;
+  const unsigned long long inc = warp_incl_scan_u64(x, lane);
+  if (lane == 31) tmp[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned long long v = lane < BLOCK / 32 ? tmp[lane] : 0ull;
+    const unsigned long long vi = warp_incl_scan_u64(v, lane);
+    if (lane < BLOCK / 32) tmp[lane] = vi - v;
+    if (lane == 31) tmp[BLOCK / 32] = vi;
   }
   __syncthreads();
-  int rmin = INT32_MAX, rmax = -1;
+  const unsigned long long r = tmp[wid] + inc - x;
+  *total = tmp[BLOCK / 32];
+  __syncthreads();
+  return r;
+}
+
+// Shared-memory layout of the bitmap kernel.
+struct BitmapSmem {
+  unsigned long long* bm;  // W64 words: row bitmap of the slab (kept zero between slabs)
+  uint16_t* wpre;          // W64: exclusive popcount prefix of each non-empty word
+  uint32_t* summ;          // NSW = max(1, W64/32): one bit per bitmap word (kept zero between slabs)
+  uint16_t* nel;           // umax: the non-empty words in row order
+  int32_t* rows;           // umax: output rows of the slab in rank order
+  unsigned char* acc;      // umax values (room for doubles)
+  unsigned long long* red; // BLOCK/32 + 1 scan slots
+  int W64, NSW, umax;
+};
+
+// Bitmap words per thread for `nwords` words: a power of two <= 32, so a
+// thread's run of words sits inside one summary word.
+template <int BLOCK>
+__device__ __forceinline__ int words_per_thread(int nwords) {
+  int per = 1;
+  while (per * BLOCK < nwords && per < 32) per <<= 1;
+  return per;
+}
+
+// The summary bits of words [w0, w0 + per) (per a power of two <= 32, w0 a multiple of per).
+__device__ __forceinline__ uint32_t own_word_mask(const uint32_t* summ, int w0, int per, int nwords) {
+  if (w0 >= nwords) return 0u;
+  const uint32_t all = summ[w0 >> 5] >> (w0 & 31);
+  return per == 32 ? all : (all & ((1u << per) - 1u));
+}
+
+// Calls f(row, value) for every entry of input segments [beg_i, beg_i + len_i)
+// of the item's inputs, 32 inputs per chunk; the warps of the block split each
+// chunk's flattened entries.  Equal-length chunks use the one-multiply map.
+template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename F>
+__device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, int off, SegF& seg, F& f) {
+  constexpr int NW = BLOCK / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int cb = 0; cb < k; cb += 32) {
     const int i = cb + lane;
     int beg = 0, len = 0;
-    if (i < k) {
-      if (W.search < 0) {
-        const int32_t* cp = in.cp[off + i];
-        beg = __ldg(cp + j);
-        len = __ldg(cp + j + 1) - beg;
-      } else {
-        const int32_t* o = offs + ((int64_t)W.search * in.kmax + i) * 2;
-        beg = o[0];
-        len = o[1] - beg;
-      }
-    }
-    SegWalk w;
-    w.init(beg, len, lane);
-    for (int e0 = wid * 32 * U; e0 < w.total; e0 += NW * 32 * U) {
+    if (i < k) seg(i, &beg, &len);
+    ChunkMap cm;
+    cm.init(beg, len, lane, min(32, k - cb));
+    for (int e0 = wid * 32 * U; e0 < cm.total; e0 += NW * 32 * U) {
       int32_t r[U];
       V v[U];
 #pragma unroll
       for (int t = 0; t < U; ++t) {
         const int e = e0 + t * 32 + lane;
-        const int seg = w.find(e);
-        const int idx = w.index_in_input(e, seg);
+        int sg;
+        const int idx = cm.locate(e, &sg);
         r[t] = -1;
         v[t] = V(0);
-        if (e < w.total) {
-          r[t] = __ldg(in.ri[off + cb + seg] + idx);
-          v[t] = __ldg(static_cast<const V*>(in.val[off + cb + seg]) + idx);
+        if (e < cm.total) {
+          r[t] = __ldg(in.ri[off + cb + sg] + idx);
+          if constexpr (VALS) v[t] = __ldg(static_cast<const V*>(in.val[off + cb + sg]) + idx);
         }
       }
 #pragma unroll
-      for (int t = 0; t < U; ++t) {
-        if (r[t] < 0) continue;
-        bool fresh;
-        const int h = table_insert_pad(keys, hash_scrambled(r[t], q), mask, r[t], fresh);
-        if (h < 0) continue;  // table full: the count check below reports it
-        atomicAdd(&vals[sp(h)], v[t]);
-        rmin = min(rmin, r[t]);
-        rmax = max(rmax, r[t]);
-      }
+      for (int t = 0; t < U; ++t)
+        if (r[t] >= 0) f(r[t], v[t]);
     }
-  }
-  rmin = warp_min(rmin);
-  rmax = warp_max(rmax);
-  if (lane == 0) {
-    atomicMin(&s_rng[0], rmin);
-    atomicMax(&s_rng[1], rmax);
-  }
-  __syncthreads();
-  rmin = s_rng[0];
-  rmax = s_rng[1];
-  // Compaction through registers: thread t owns slots [t*S, t*S + S).
-  const int S = T >= BLOCK ? T / BLOCK : 1;
-  const int p0 = threadIdx.x * S;
-  int32_t kk[SMAX];
-  V vv[SMAX];
-  int mine = 0;
-#pragma unroll
-  for (int t = 0; t < SMAX; ++t) {
-    kk[t] = -1;
-    vv[t] = V(0);
-    if (t < S && p0 + t < T) {
-      kk[t] = keys[sp(p0 + t)];
-      vv[t] = vals[sp(p0 + t)];
-      mine += kk[t] >= 0;
-    }
-  }
-  int tot;
-  int dst = block_excl_scan<BLOCK>(mine, red, &tot);  // synchronises: all reads are done
-  const bool ok = (tot == u);
-  if (ok) {
-#pragma unroll
-    for (int t = 0; t < SMAX; ++t)
-      if (kk[t] >= 0) {
-        keys[sp(dst)] = kk[t];
-        vals[sp(dst)] = vv[t];
-        ++dst;
-      }
-  } else if (threadIdx.x == 0) {
-    atomicOr(&ctr_w->err, ERR_INTERNAL);
-  }
-  __syncthreads();
-  if (!ok) return;
-  const int NB = T / 2;
-  const uint32_t span = (uint32_t)(rmax - rmin) + 1u;
-  const uint64_t bmul = ((uint64_t)NB << 32) / span;
-  for (int x = threadIdx.x; x < u; x += BLOCK) add16p(cnt, bucket_of(keys[sp(x)], rmin, bmul));
-  __syncthreads();
-  block_scan16p<BLOCK>(cnt, NB, red);
-  __syncthreads();
-  for (int x = threadIdx.x; x < u; x += BLOCK) {
-    const int32_t key = keys[sp(x)];
-    const int pos = (int)add16p(cnt, bucket_of(key, rmin, bmul));
-    keys[sp(T / 2 + pos)] = key;
-    vals[sp(T / 2 + pos)] = vals[sp(x)];
-  }
-  __syncthreads();
-  for (int x = threadIdx.x; x < u; x += BLOCK) {
-    const int32_t key = keys[sp(T / 2 + x)];
-    const uint32_t b = bucket_of(key, rmin, bmul);
-    const int lo = b ? (int)get16p(cnt, b - 1u) : 0;
-    const int hi = (int)get16p(cnt, b);
-    int rank = lo;
-    for (int y = lo; y < hi; ++y) rank += keys[sp(T / 2 + y)] < key;
-    out_row[rank] = key;
-    out_val[rank] = vals[sp(T / 2 + x)];
   }
 }
 
+// One item (a CTA-class column or a heavy column's row window [r_lo, r_hi),
+// Alg. 8: B(r1:r2, j) <- HashAdd(A_1(r1:r2, j), ..., A_k(r1:r2, j))).
+template <typename V, int BLOCK, int U>
+__device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, const Inst* I, const int32_t* offs,
+                                            int32_t* __restrict__ out_row, V* __restrict__ out_val,
+                                            const BitmapSmem& sm, int slab_log2, Counters* ctr_w) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int k = I->k, off = I->ptr_off, j = W.col - I->colbase;
+  V* acc = reinterpret_cast<V*>(sm.acc);
+  const int64_t S = (int64_t)1 << slab_log2;
+  const int64_t span = (int64_t)W.r_hi - W.r_lo;
+  const int nsl = span <= 0 ? 0 : (int)((span + S - 1) >> slab_log2);
+  int u_done = 0;
+  bool bad = false;
+  for (int t = 0; t < nsl; ++t) {
+    const int lo = W.r_lo + (int)(t * S);
+    const int hi = (int)min((int64_t)W.r_hi, (int64_t)lo + S);
+    const uint32_t width = (uint32_t)(hi - lo);
+    // The item's entries of input i that fall in [lo, hi).
+    auto seg = [&](int i, int* beg, int* len) {
+      int b, e;
+      if (W.search < 0) {
+        const int32_t* cp = in.cp[off + i];
+        b = __ldg(cp + j);
+        e = __ldg(cp + j + 1);
+      } else {
+        const int32_t* o = offs + ((int64_t)W.search * in.kmax + i) * 2;
+        b = o[0];
+        e = o[1];
+      }
+      if (nsl > 1) {
+        const int32_t* ri = in.ri[off + i];
+        b = lower_bound_i32(ri, b, e, lo);
+        e = lower_bound_i32(ri, b, e, hi);
+      }
+      *beg = b;
+      *len = e - b;
+    };
+    // Pass A: row bits (rows outside the slab are ignored: they cannot occur
+    // for valid inputs, and shared-memory accesses stay in bounds).
+    auto setbit = [&](int32_t r, V) {
+      const uint32_t rr = (uint32_t)(r - lo);
+      if (rr < width) {
+        const uint32_t w = rr >> 6;
+        if (set_row_bit(sm.bm, rr)) atomicOr(&sm.summ[w >> 5], 1u << (w & 31));
+      }
+    };
+    block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, setbit);
+    __syncthreads();
+    // Rank prefix: thread t owns bitmap words [t*per, t*per + per); their
+    // non-empty ones are the set bits of `mine` (kept for the clear below).
+    const int nwords = (int)((width + 63) >> 6);
+    const int per = words_per_thread<BLOCK>(nwords);
+    const int w0 = threadIdx.x * per;
+    const uint32_t mine = own_word_mask(sm.summ, w0, per, nwords);
+    unsigned long long loc = (unsigned long long)__popc(mine) << 32;  // (non-empty words << 32) | rows
+    for (uint32_t bits = mine; bits; bits &= bits - 1) loc += (unsigned long long)__popcll(sm.bm[w0 + __ffs(bits) - 1]);
+    unsigned long long tot;
+    const unsigned long long ex = block_excl_scan_u64<BLOCK>(loc, sm.red, &tot);
+    const int slab_u = (int)(tot & 0xffffffffull);
+    const int slab_ne = (int)(tot >> 32);
+    const bool fits = u_done + slab_u <= sm.umax && !bad;
+    if (fits) {
+      int rank = (int)(ex & 0xffffffffull), pos = (int)(ex >> 32);
+      for (uint32_t bits = mine; bits; bits &= bits - 1) {
+        const int w = w0 + __ffs(bits) - 1;
+        sm.wpre[w] = (uint16_t)rank;
+        sm.nel[pos++] = (uint16_t)w;
+        rank += __popcll(sm.bm[w]);
+      }
+      for (int q = threadIdx.x; q < slab_u; q += BLOCK) acc[q] = V(0);
+    } else {
+      bad = true;
+    }
+    __syncthreads();
+    if (fits) {
+      // Pass B: values at their rank.
+      auto add = [&](int32_t r, V v) {
+        const uint32_t rr = (uint32_t)(r - lo);
+        if (rr < width) {
+          const uint32_t w = rr >> 6;
+          const unsigned long long bits = sm.bm[w];
+          const uint32_t below = rr & 63;
+          const int q = (int)sm.wpre[w] + __popcll(below ? (bits << (64 - below)) : 0ull);
+          if (bits && q < slab_u) atomicAdd(&acc[q], v);
+        }
+      };
+      block_for_each_entry<true, V, BLOCK, U>(in, k, off, seg, add);
+      // Rows in rank order: one thread per non-empty word.
+      for (int p = threadIdx.x; p < slab_ne; p += BLOCK) {
+        const int w = sm.nel[p];
+        int q = sm.wpre[w];
+        const int rbase = lo + (w << 6);
+        for (unsigned long long bits = sm.bm[w]; bits; bits &= bits - 1) sm.rows[q++] = rbase + __ffsll(bits) - 1;
+      }
+      __syncthreads();
+      // Coalesced write of the slab's rows and values.  Ranks past the
+      // symbolic count are never written (B holds W.u rows here); they can
+      // only arise if the inputs changed between the passes.
+      const int lim = min(slab_u, W.u - u_done);
+      int32_t* orow = out_row + u_done;
+      V* oval = out_val + u_done;
+      for (int q = threadIdx.x; q < lim; q += BLOCK) {
+        orow[q] = sm.rows[q];
+        oval[q] = acc[q];
+      }
+      u_done += slab_u;
+    }
+    // Clear this thread's words; then the summary.
+    for (uint32_t bits = mine; bits; bits &= bits - 1) sm.bm[w0 + __ffs(bits) - 1] = 0ull;
+    __syncthreads();
+    for (int x = threadIdx.x; x < ((nwords + 31) >> 5); x += BLOCK) sm.summ[x] = 0u;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && (bad || u_done != W.u)) atomicOr(&ctr_w->err, ERR_INTERNAL);
+}
+
 // DT: 0 = every problem float, 1 = every problem double, 2 = per-problem dtype.
-template <int DT, int BLOCK, int U, int SMAX>
-__global__ void __launch_bounds__(BLOCK) k_num_cta(Inputs in, const Window* __restrict__ win, int nwin,
-                                                   const int32_t* __restrict__ offs,
-                                                   const int64_t* __restrict__ col_ptr, Outs o, int tmax,
-                                                   Counters* ctr_w) {
+template <int DT, int BLOCK, int U>
+__global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* __restrict__ win, int nwin,
+                                                      const int32_t* __restrict__ offs,
+                                                      const int64_t* __restrict__ col_ptr, Outs o, int slab_log2,
+                                                      int umax, Counters* ctr_w) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ int red[BLOCK / 32 + 1];
-  __shared__ int s_rng[2];
+  __shared__ unsigned long long red[BLOCK / 32 + 1];
+  BitmapSmem sm;
+  sm.W64 = 1 << (slab_log2 - 6);
+  sm.NSW = (sm.W64 + 31) >> 5;
+  sm.umax = umax;
+  sm.bm = reinterpret_cast<unsigned long long*>(sm_raw);
+  sm.acc = reinterpret_cast<unsigned char*>(sm.bm + sm.W64);
+  sm.wpre = reinterpret_cast<uint16_t*>(sm.acc + (size_t)umax * 8);
+  sm.summ = reinterpret_cast<uint32_t*>(sm.wpre + ((sm.W64 + 1) & ~1));
+  sm.rows = reinterpret_cast<int32_t*>(sm.summ + sm.NSW);
+  sm.nel = reinterpret_cast<uint16_t*>(sm.rows + umax);
+  sm.red = red;
+  for (int x = threadIdx.x; x < sm.W64; x += BLOCK) sm.bm[x] = 0ull;
+  for (int x = threadIdx.x; x < sm.NSW; x += BLOCK) sm.summ[x] = 0u;
+  __syncthreads();
   for (int wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
     const Window W = win[wi];
     const int q = inst_of(in, W.col);
@@ -233,24 +272,17 @@ __global__ void __launch_bounds__(BLOCK) k_num_cta(Inputs in, const Window* __re
     const int64_t out = col_ptr[W.col] - (in.col_inst ? col_ptr[I->colbase] : 0) + W.out_off;
     int32_t* out_row = out_row_of(o, q) + out;
     if (DT == 1 || (DT == 2 && I->dtype == 1))
-      cta_item<double, BLOCK, U, SMAX>(in, W, I, offs, out_row, static_cast<double*>(out_val_of(o, q)) + out,
-                                       sm_raw, tmax, red, s_rng, ctr_w);
+      bitmap_item<double, BLOCK, U>(in, W, I, offs, out_row, static_cast<double*>(out_val_of(o, q)) + out, sm,
+                                    slab_log2, ctr_w);
     else
-      cta_item<float, BLOCK, U, SMAX>(in, W, I, offs, out_row, static_cast<float*>(out_val_of(o, q)) + out,
-                                      sm_raw, tmax, red, s_rng, ctr_w);
-    __syncthreads();
+      bitmap_item<float, BLOCK, U>(in, W, I, offs, out_row, static_cast<float*>(out_val_of(o, q)) + out, sm,
+                                   slab_log2, ctr_w);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
-static int pow2_at_least(int x) {
-  int p = 1;
-  while (p < x) p <<= 1;
-  return p;
-}
-
 static int blocks_per_sm(const DeviceInfo& dev, size_t smem_per_block, int threads_per_block) {
   const size_t reserve = 1024;
   int b = (int)(dev.smem_per_sm / (smem_per_block + reserve));
@@ -260,24 +292,40 @@ static int blocks_per_sm(const DeviceInfo& dev, size_t smem_per_block, int threa
   return b < 1 ? 1 : b;
 }
 
-template <int DT>
-static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_win, const int32_t* offs,
-                                    const int64_t* col_ptr, const Outs& out, int window_max, Counters* ctr_w,
-                                    const DeviceInfo& dev, cudaStream_t st) {
-  using V = typename std::conditional<DT == 0, float, double>::type;  // value bytes per slot
-  constexpr int BLOCK = 512;
-  constexpr int SMAX = 2 * WINDOW_MAX_LIMIT / BLOCK;  // 16 slots per thread at the largest table
-  const int tmax = pow2_at_least(2 * window_max);
-  const size_t slots = (size_t)tmax + tmax / 32;
-  const size_t smem = slots * (sizeof(V) + 4) + (size_t)cw(tmax / 4) * 4 + 16;
-  auto kern = k_num_cta<DT, BLOCK, 4, SMAX>;
+// Shared bytes of the bitmap kernel for a slab of 2^slab_log2 rows and umax ranks.
+static size_t bitmap_smem_bytes(int slab_log2, int umax) {
+  const size_t w64 = (size_t)1 << (slab_log2 - 6);
+  const size_t nsw = (w64 + 31) / 32;
+  return w64 * 8 + (size_t)umax * 8 + ((w64 + 1) & ~(size_t)1) * 2 + nsw * 4 + (size_t)umax * 4 +
+         (size_t)umax * 2 + 16;
+}
+
+template <int DT, int BLOCK>
+static cudaError_t launch_bitmap_t(const Inputs& in, const Window* win, int n_win, const int32_t* offs,
+                                   const int64_t* col_ptr, const Outs& out, int slab_log2, int umax, size_t smem,
+                                   Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+  auto kern = k_num_bitmap<DT, BLOCK, 4>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int grid = dev.sms * blocks_per_sm(dev, smem, BLOCK);
+  int grid = dev.sms * blocks_per_sm(dev, smem + sizeof(unsigned long long) * (BLOCK / 32 + 1), BLOCK);
   if (grid > n_win) grid = n_win;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, BLOCK, smem, st>>>(in, win, n_win, offs, col_ptr, out, tmax, ctr_w);
+  kern<<<grid, BLOCK, smem, st>>>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, ctr_w);
   return cudaGetLastError();
+}
+
+template <int DT>
+static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_win, const int32_t* offs,
+                                    const int64_t* col_ptr, const Outs& out, int umax, Counters* ctr_w,
+                                    const DeviceInfo& dev, cudaStream_t st) {
+  int slab_log2 = 10;
+  while (slab_log2 < NUM_SLAB_LOG2_MAX && ((int64_t)1 << slab_log2) < (int64_t)in.mmax) ++slab_log2;
+  const size_t smem = bitmap_smem_bytes(slab_log2, umax);
+  if (smem > (size_t)dev.smem_optin) return cudaErrorInvalidConfiguration;
+  // Small bitmaps leave room for several blocks per SM: use 512 threads.
+  if (smem <= (size_t)dev.smem_per_sm / 2 - 2048)
+    return launch_bitmap_t<DT, 512>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, smem, ctr_w, dev, st);
+  return launch_bitmap_t<DT, 1024>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, smem, ctr_w, dev, st);
 }
 
 cudaError_t launch_num_cta(const Inputs& in, int dt, const Window* win, int n_win, const int32_t* offs,

@@ -4,11 +4,11 @@
 // CTA class (s_j <= cta_max): one thread block per column, same table with the
 //   scrambled (multiplicative) hash.  Emits one numeric work item per column.
 // Heavy class: one thread block per column with a shared-memory bitmap of a
-//   2^20-row slab (the dense-accumulator form of the symbolic step, which
-//   Sec. II-D allows in place of the hash).  Popcounts give nnz(B(:,j)) and
-//   cut the column into row windows of at most window_max distinct rows each
-//   (Alg. 7/8's sliding windows, sized to shared memory and balanced by count
-//   rather than by equal row ranges).
+//   slab of up to 2^20 rows (the dense-accumulator form of the symbolic step,
+//   which Sec. II-D allows in place of the hash).  Popcounts give nnz(B(:,j))
+//   and cut the column into row windows of fewer than window_max distinct rows
+//   each (Alg. 7/8's sliding windows, sized to shared memory and balanced by
+//   count rather than by equal row ranges).
 #include "spk_common.cuh"
 #include "spk_launch.h"
 
@@ -97,27 +97,36 @@ __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __r
 }
 
 constexpr int HEAVY_BLOCK = 1024;
+constexpr int MAX_SLAB_WINDOWS = 1100;  // 2^20 rows / (1024 - 64) + 2
 
-// The bitmap keeps one pad word after every 32: a thread that scans 32
-// consecutive words then starts on its own bank.
-__device__ __forceinline__ int bm_pad(int w) { return w + (w >> 5); }
-constexpr int MAX_SLAB_WINDOWS = 1100;  // (2^20 rows / 32 bits per word) / (1024 - 32) + 2
-
+// Heavy columns: one thread block per column.  Rows of one slab of 2^20 rows
+// at a time go into a 64-bit-word bitmap plus a summary bitmap (one bit per
+// non-empty word), both kept zero between slabs, so the work per slab grows
+// with the rows present, not with the slab.  The popcount prefix over the
+// non-empty words gives nnz(B(:,j)) and cuts the column into windows of at
+// most win_target + 63 distinct rows (boundaries on 64-row words).
 template <int BLOCK, int U>
 __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* __restrict__ list,
                                                      const Counters* __restrict__ ctr, int32_t* __restrict__ u_out,
                                                      Window* __restrict__ win, int32_t* __restrict__ search_list,
-                                                     int64_t win_cap, int win_target, int slab_words,
+                                                     int64_t win_cap, int win_target, int slab_log2,
                                                      Counters* ctr_w) {
-  extern __shared__ uint32_t bm[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int red[BLOCK / 32 + 1];
   __shared__ int bnd[MAX_SLAB_WINDOWS + 1];
   __shared__ int cval[MAX_SLAB_WINDOWS + 1];
   __shared__ int s_col_u, s_wbase, s_sbase;
   constexpr int NW = BLOCK / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int W64 = 1 << (slab_log2 - 6);
+  const int NSW = (W64 + 31) >> 5;
+  unsigned long long* bm = reinterpret_cast<unsigned long long*>(sm_raw);
+  uint32_t* summ = reinterpret_cast<uint32_t*>(bm + W64);
+  for (int x = threadIdx.x; x < W64; x += BLOCK) bm[x] = 0ull;
+  for (int x = threadIdx.x; x < NSW; x += BLOCK) summ[x] = 0u;
+  __syncthreads();
   const int ncols = ctr->n_heavy;
-  const int slab_rows = slab_words * 32;
+  const int slab_rows = 1 << slab_log2;
   for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
     const int g = list[c];
     const Inst* I = in.inst + inst_of(in, g);
@@ -127,13 +136,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
     for (int slab = 0; slab < nslabs; ++slab) {
       const int lo = slab * slab_rows;
       const int hi = (int)min((int64_t)m, (int64_t)lo + slab_rows);
-      const int words = (hi - lo + 31) >> 5;
-      {
-        uint4* bm4 = reinterpret_cast<uint4*>(bm);
-        const int w4 = (bm_pad(words) + 3) >> 2;  // the bitmap buffer is rounded up to whole uint4
-        for (int p = threadIdx.x; p < w4; p += BLOCK) bm4[p] = make_uint4(0u, 0u, 0u, 0u);
-      }
-      __syncthreads();
+      const uint32_t width = (uint32_t)(hi - lo);
       for (int cb = 0; cb < k; cb += 32) {
         const int i = cb + lane;
         int beg = 0, len = 0;
@@ -148,32 +151,43 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
           beg = b;
           len = e - b;
         }
-        SegWalk w;
-        w.init(beg, len, lane);
-        for (int e0 = wid * 32 * U; e0 < w.total; e0 += NW * 32 * U) {
+        ChunkMap cm;
+        cm.init(beg, len, lane, min(32, k - cb));
+        for (int e0 = wid * 32 * U; e0 < cm.total; e0 += NW * 32 * U) {
           int32_t r[U];
 #pragma unroll
           for (int t = 0; t < U; ++t) {
             const int e = e0 + t * 32 + lane;
-            const int seg = w.find(e);
-            const int idx = w.index_in_input(e, seg);
+            int sg;
+            const int idx = cm.locate(e, &sg);
             r[t] = -1;
-            if (e < w.total) r[t] = __ldg(in.ri[off + cb + seg] + idx);
+            if (e < cm.total) r[t] = __ldg(in.ri[off + cb + sg] + idx);
           }
 #pragma unroll
           for (int t = 0; t < U; ++t) {
-            const int rr = r[t] - lo;
-            if (r[t] >= 0 && rr < hi - lo) atomicOr(&bm[bm_pad(rr >> 5)], 1u << (rr & 31));
+            const uint32_t rr = (uint32_t)(r[t] - lo);
+            if (r[t] >= 0 && rr < width) {
+              const uint32_t w = rr >> 6;
+              if (set_row_bit(bm, rr)) atomicOr(&summ[w >> 5], 1u << (w & 31));
+            }
           }
         }
       }
       __syncthreads();
-      // Popcount prefix over the slab's words (thread t owns a contiguous run).
-      const int per = (words + BLOCK - 1) / BLOCK;
+      // Popcount prefix over the non-empty words: thread t owns bitmap words
+      // [t*per, t*per + per) (a power of two <= 32, inside one summary word);
+      // `mine` holds which of them are non-empty.
+      const int nwords = (int)((width + 63) >> 6);
+      int per = 1;
+      while (per * BLOCK < nwords && per < 32) per <<= 1;
       const int w0 = threadIdx.x * per;
+      uint32_t mine = 0u;
+      if (w0 < nwords) {
+        mine = summ[w0 >> 5] >> (w0 & 31);
+        if (per < 32) mine &= (1u << per) - 1u;
+      }
       int loc = 0;
-      for (int t = 0; t < per; ++t)
-        if (w0 + t < words) loc += __popc(bm[bm_pad(w0 + t)]);
+      for (uint32_t bits = mine; bits; bits &= bits - 1) loc += __popcll(bm[w0 + __ffs(bits) - 1]);
       int slab_u;
       const int ex = block_excl_scan<BLOCK>(loc, red, &slab_u);
       const int P = slab_u == 0 ? 0 : (slab_u + win_target - 1) / win_target;
@@ -184,21 +198,24 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
         if (threadIdx.x == 0) {
           bnd[0] = 0;
           cval[0] = 0;
-          bnd[P] = words;
+          bnd[P] = nwords;
           cval[P] = slab_u;
           s_wbase = atomicAdd(&ctr_w->n_windows, P);
           s_sbase = whole ? -1 : atomicAdd(&ctr_w->n_search, P);
         }
-        int run = ex;
-        for (int t = 0; t < per; ++t) {
-          const int wd = w0 + t;
-          if (wd >= words) break;
-          const int before = run;
-          run += __popc(bm[bm_pad(wd)]);
-          const int pb = before / win_target, pa = run / win_target;
-          if (pa > pb && pa >= 1 && pa <= P - 1) {
-            bnd[pa] = wd + 1;
-            cval[pa] = run;
+        // Window p starts after the word in which the running count first
+        // reaches p * win_target.
+        if (P > 1) {
+          int run = ex;
+          for (uint32_t bits = mine; bits; bits &= bits - 1) {
+            const int wd = w0 + __ffs(bits) - 1;
+            const int before = run;
+            run += __popcll(bm[wd]);
+            const int pb = before / win_target, pa = run / win_target;
+            if (pa > pb && pa >= 1 && pa <= P - 1) {
+              bnd[pa] = wd + 1;
+              cval[pa] = run;
+            }
           }
         }
         __syncthreads();
@@ -208,8 +225,8 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
           if (wi < win_cap && (whole || s_sbase + p < win_cap)) {
             Window w;
             w.col = g;
-            w.r_lo = whole ? 0 : lo + 32 * bnd[p];
-            w.r_hi = whole ? m : (int)min((int64_t)hi, (int64_t)lo + 32 * (int64_t)bnd[p + 1]);
+            w.r_lo = whole ? 0 : lo + 64 * bnd[p];
+            w.r_hi = whole ? m : (int)min((int64_t)hi, (int64_t)lo + 64 * (int64_t)bnd[p + 1]);
             w.u = cval[p + 1] - cval[p];
             w.out_off = col_u + cval[p];
             w.search = whole ? -1 : s_sbase + p;
@@ -220,7 +237,10 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
           }
         }
       }
+      // Clear this thread's words, then the summary, for the next slab or column.
+      for (uint32_t bits = mine; bits; bits &= bits - 1) bm[w0 + __ffs(bits) - 1] = 0ull;
       __syncthreads();
+      for (int x = threadIdx.x; x < ((nwords + 31) >> 5); x += BLOCK) summ[x] = 0u;
       if (threadIdx.x == 0) s_col_u += slab_u;
       __syncthreads();
     }
@@ -264,16 +284,17 @@ cudaError_t launch_sym_cta(const Inputs& in, const int32_t* list, const int32_t*
 cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counters* ctr, int32_t* u, Window* win,
                              int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
                              const DeviceInfo& dev, cudaStream_t st) {
-  const int slab_rows = (int)(in.mmax < (1 << SLAB_BITS) ? in.mmax : (1 << SLAB_BITS));
-  const int slab_words = (slab_rows + 31) / 32 > 0 ? (slab_rows + 31) / 32 : 1;
-  const int padded = slab_words + slab_words / 32 + 1;
-  const size_t smem = (size_t)((padded + 3) / 4 * 4) * sizeof(uint32_t);
+  int slab_log2 = 10;
+  while (slab_log2 < SLAB_BITS && ((int64_t)1 << slab_log2) < (int64_t)in.mmax) ++slab_log2;
+  const size_t w64 = (size_t)1 << (slab_log2 - 6);
+  const size_t smem = w64 * 8 + ((w64 + 31) / 32) * 4 + 16;
   auto kern = k_sym_heavy<HEAVY_BLOCK, 4>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const size_t static_smem = sizeof(int) * (2 * (MAX_SLAB_WINDOWS + 1) + HEAVY_BLOCK / 32 + 4);
   const int grid = dev.sms * blocks_per_sm(dev, smem + static_smem, HEAVY_BLOCK);
-  kern<<<grid, HEAVY_BLOCK, smem, st>>>(in, list, ctr, u, win, search_list, win_cap, window_max - 32, slab_words,
+  // Windows end on 64-row words: a window holds at most win_target + 63 rows.
+  kern<<<grid, HEAVY_BLOCK, smem, st>>>(in, list, ctr, u, win, search_list, win_cap, window_max - 64, slab_log2,
                                         ctr_w);
   return cudaGetLastError();
 }
