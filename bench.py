@@ -645,13 +645,121 @@ def run_batch(args, world, rank, local):
     print(json.dumps(out))
 
 
+# ---------------------------------------------------------------------------
+# Served workload: Poisson arrivals of requests drawn like the batched workload
+# but with k log-uniform on [2, 512] and m = n log-uniform on [2^10, 2^18].
+# The inputs of every request stay on the device before it arrives, and all
+# requests of the full stream (about 2.9e12 input nonzeros) do not fit HBM,
+# so requests reuse the inputs of a pool: the longest prefix of the seeded
+# stream whose inputs fit the pool budget.  Request r computes the sum of pool
+# entry r mod G.  The capacity C (requests/s) is the pool run as one burst; the
+# trace runs at fractions of C, with continuous batching and with one batch
+# per request, and every request's output digest is checked against the same
+# problem computed alone.
+# ---------------------------------------------------------------------------
+SERVE_WORKLOAD = "serve_k2-512_mn2p10-2p18_L4-64"
+
+
+def run_serve(args, world, rank, local):
+    import numpy as np
+
+    import paper_2112_10223_gb300 as spk
+    import synth
+    from paper_2112_10223_gb300.serve import Request, Server, output_digest
+
+    spk.library()
+    if rank != 0:
+        return
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    params = synth.batch_instance_params(args.serve_requests, seed=args.seed, k_range=(2, 512),
+                                         mn_range=(1 << 10, 1 << 18))
+    free, _ = torch.cuda.mem_get_info()
+    pool_budget = int(free * args.serve_pool_frac)
+    pool, used = [], 0
+    for q, p in enumerate(params):  # the longest seed-order prefix that fits: an unbiased sample
+        if len(pool) >= args.serve_pool_max:
+            break
+        b = synth.instance_nnz_estimate(p) * (4 + (8 if p["dtype"] == torch.float64 else 4))
+        if used + b > pool_budget:
+            break
+        A, m = synth.instance(p, device=dev)
+        pool.append((A, m, q))
+        used += sum(a[1].numel() * (4 + a[2].element_size()) for a in A) + A[0][0].numel() * 4
+    torch.cuda.synchronize()
+    G = len(pool)
+    pool_nnz = [sum(a[1].numel() for a in A) for A, _, _ in pool]
+    # Alone results of every pool entry (digest only).
+    alone = []
+    for A, m, _ in pool:
+        alone.append(output_digest(spk.spkadd(A, m)))
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.8)
+
+    def trace(rate, count, seed):
+        rng = np.random.default_rng(seed)
+        t = np.cumsum(rng.exponential(1.0 / rate, size=count)) if rate > 0 else np.zeros(count)
+        return [Request(r, pool[r % G][0], pool[r % G][1], arrival=float(t[r]), tag=r % G) for r in range(count)]
+
+    # Capacity: the pool as one burst (all arrive at 0), after one warm-up burst.
+    Server(dev, budget).run(trace(0, G, 1))
+    burst = Server(dev, budget).run(trace(0, G, 1))
+    cap = G / burst.seconds
+    burst1 = Server(dev, budget, batching=False).run(trace(0, G, 1))
+    cap1 = G / burst1.seconds
+
+    results = []
+    R = args.serve_requests
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for frac in args.serve_rates:
+        rate = frac * cap
+        st_b = Server(dev, budget).run(trace(rate, R, 100 + int(frac * 100)))
+        st_1 = Server(dev, budget, batching=False).run(trace(rate, R, 100 + int(frac * 100)))
+        results.append({"load": frac, "rate_per_s": rate, "batched": st_b.summary(), "per_request": st_1.summary()})
+    clk = clocks.stop()
+
+    # Alone vs mix: every request of a trace at the highest load, digests compared.
+    bad = []
+    tol = {torch.float64: 1e-12, torch.float32: 1e-5}
+
+    def check(r):
+        d = output_digest(r.out)
+        a = alone[r.tag]
+        scale = max(a[3], 1e-300)
+        if d[0] != a[0] or d[1] != a[1] or abs(d[2] - a[2]) > tol[r.dtype] * max(scale, 1.0) * 4:
+            bad.append(r.rid)
+
+    vr = max(args.serve_rates) * cap
+    Server(dev, budget, on_done=check).run(trace(vr, R, 999))
+    if bad:
+        raise SystemExit(f"alone-vs-mix digest mismatch for requests {bad[:10]}")
+
+    hi = results[-1]
+    out = {
+        "metric": METRIC, "value": hi["batched"]["nnz_per_s"], "unit": "nnz/s", "n_gpus": world,
+        "steps": len(args.serve_rates), "warmup": 1, "ms_per_step": hi["batched"]["seconds"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD, "requests_per_trace": R, "pool_instances": G,
+                   "pool_input_nnz": int(sum(pool_nnz)),
+                   "pool_budget_bytes": pool_budget, "serve_budget_bytes": budget, "seed": args.seed},
+        "serve": {"capacity_req_per_s": cap, "capacity_per_request_req_per_s": cap1,
+                  "burst_batches": burst.batches, "loads": results,
+                  "alone_vs_mix": {"requests": R, "load": max(args.serve_rates), "mismatches": len(bad)}},
+        "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+        "gpu_launches": None,
+    }
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD], default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, SERVE_WORKLOAD],
+                    default=DEFAULT_WORKLOAD)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--oracle-cols", type=int, default=1 << 19)
@@ -659,6 +767,11 @@ def main():
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--batch-mem-frac", type=float, default=0.55, help="device memory share of one wave")
     ap.add_argument("--batch-verify", type=int, default=2, help="instances per wave checked against the oracle")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests per served trace")
+    ap.add_argument("--serve-pool-frac", type=float, default=0.3, help="device memory share of the input pool")
+    ap.add_argument("--serve-pool-max", type=int, default=512, help="most distinct requests in the input pool")
+    ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")], default=[0.5, 0.7, 0.9],
+                    help="loads as fractions of the measured capacity")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -667,6 +780,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == BATCH_WORKLOAD:
         run_batch(args, world, rank, local)
+    elif args.workload == SERVE_WORKLOAD:
+        run_serve(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

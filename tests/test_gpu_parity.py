@@ -281,3 +281,36 @@ def test_rmat_k64_scale20_fp32_sampled():
     check_global_invariants(A, B, 1 << 20)
     cols, _ = sample_columns(A, 3000, 48, seed=2)
     check_sampled(A, B, 1 << 20, cols, F32)
+
+
+@pytest.mark.parametrize("dtype,kind", [(F64, "int8"), (F64, "uniform"), (F32, "uniform")])
+def test_register_path_equal_short_segments(dtype, kind):
+    """k = 32 inputs of 16 rows per column (16-byte aligned segments): the register-resident warp path."""
+    A = synth.er(32, 4096, 1500, 16, seed=11, dtype=dtype, value_kind=kind)
+    info, _ = check_full(A, 4096, dtype, exact=(kind == "int8"))
+    assert info["cols_warp"] == 1500
+
+
+def _cap_columns(A, cap):
+    """Keep the first `cap` rows of every column (pure data movement)."""
+    out = []
+    for cp, ri, va in A:
+        cpl = cp.to(torch.int64)
+        ln = torch.clamp(cpl[1:] - cpl[:-1], max=cap)
+        keep = torch.zeros(ri.numel(), dtype=torch.bool)
+        for j in range(cp.numel() - 1):
+            keep[int(cpl[j]):int(cpl[j]) + int(ln[j])] = True
+        ncp = torch.zeros_like(cpl)
+        ncp[1:] = torch.cumsum(ln, 0)
+        out.append((ncp.to(torch.int32), ri[keep], va[keep]))
+    return out
+
+
+@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_register_path_ragged_unaligned_segments(dtype, sort_mode):
+    """k = 32 inputs, lengths 0..16 varying per input and column (unaligned starts: scalar loads)."""
+    A = _cap_columns(synth.random_csc(32, 256, 500, density=0.04, seed=12, dtype=dtype, empty_col_frac=0.05), 16)
+    lens = torch.stack([a[0][1:] - a[0][:-1] for a in A])
+    assert int(lens.max()) == 16 and int(lens.min()) == 0
+    check_full(A, 256, dtype, options=spk.default_options(sort_mode=sort_mode))
