@@ -170,18 +170,20 @@ def oracle_sample(A, cols):
     return [tuple(t.cpu() for t in a) for a in sub], stride
 
 
-def time_oracle(A, threads=0, repeat=1):
+def time_oracle(A, threads=0, repeat=1, min_seconds=0.0):
+    """Mean time of the oracle on A over `repeat` runs, or over as many runs as
+    it takes to reach min_seconds of CPU work (at most 8)."""
     import oracle
 
     An = [tuple(t.numpy() for t in a) for a in A]
     oracle.add(An, threads=threads)  # warm (page faults, build)
     ts = []
-    for _ in range(repeat):
+    while len(ts) < repeat or (sum(ts) < min_seconds and len(ts) < 8):
         t0 = time.perf_counter()
         oracle.add(An, threads=threads)
         ts.append(time.perf_counter() - t0)
     nnz = sum(a[1].numel() for a in A)
-    return nnz, min(ts), oracle.threads_used(threads)
+    return nnz, sum(ts) / len(ts), oracle.threads_used(threads), len(ts)
 
 
 def dist_setup():
@@ -229,7 +231,7 @@ def run_reference(args, world, rank):
     ts = []
     cores = 1
     for _ in range(args.steps):
-        _, t, cores = time_oracle(S, repeat=1)
+        _, t, cores, _ = time_oracle(S, repeat=1)
         ts.append(t)
     t = sum(ts) / len(ts)
     val = nnz / t
@@ -354,10 +356,10 @@ def run_ours(args, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and args.oracle_cols > 0:
         S = cpu_sample
-        nz_s, t_s, cores = time_oracle(S)
+        nz_s, t_s, cores, reps = time_oracle(S, min_seconds=10.0)
         cpu = {"value": nz_s / t_s, "unit": "nnz/s", "cores": cores, "kind": "oracle",
-               "sample": f"every {cpu_stride}-th column of the workload: {len(S[0][0]) - 1} columns, "
-                         f"{nz_s} input nnz, {t_s:.2f} s"}
+               "sample": f"every {cpu_stride}-th column of the workload ({len(S[0][0]) - 1} columns, "
+                         f"{nz_s} input nnz), {reps} runs of {t_s:.2f} s each"}
 
     if rank != 0:
         return
@@ -762,7 +764,8 @@ def main():
                     default=DEFAULT_WORKLOAD)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--oracle-cols", type=int, default=1 << 19)
+    ap.add_argument("--oracle-cols", type=int, default=1 << 20,
+                    help="columns of the CPU oracle's sample (every (n / cols)-th column)")
     ap.add_argument("--info", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--batch-mem-frac", type=float, default=0.55, help="device memory share of one wave")

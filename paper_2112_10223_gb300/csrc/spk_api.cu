@@ -491,11 +491,11 @@ static spkadd_status run_numeric(spkadd_handle* h, const spk::Outs& out) {
     ce = spk::launch_num_cta(h->in, h->dt_mode, h->d_win, cta_items, h->d_offs, h->d_colptr, out,
                              h->opt.window_max > h->opt.cta_max ? h->opt.window_max : h->opt.cta_max, h->d_ctr,
                              h->dev, h->st);
-  h->launches += cta_items > 0;
+  h->launches += (cta_items > 0) * (h->dt_mode == 2 ? 2 : 1);
   if (ce == cudaSuccess && h->h_ctr.n_warp > 0)
     ce = spk::launch_num_warp(h->in, h->dt_mode, h->d_wl, h->d_ctr, h->h_ctr.n_warp, h->d_s, h->d_u, h->d_colptr,
                               out, h->opt.warp_max, h->opt.sort_mode, h->d_ctr, h->dev, h->st);
-  h->launches += h->h_ctr.n_warp > 0;
+  h->launches += (h->h_ctr.n_warp > 0) * (h->dt_mode == 2 ? 2 : 1);
   return from_cuda(ce);
 }
 

@@ -243,12 +243,13 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
   if (threadIdx.x == 0 && (bad || u_done != W.u)) atomicOr(&ctr_w->err, ERR_INTERNAL);
 }
 
-// DT: 0 = every problem float, 1 = every problem double, 2 = per-problem dtype.
+// DT: 0 = float values, 1 = double values.  A batch mixing both runs the
+// kernel once per dtype; only_dtype >= 0 then skips the other dtype's items.
 template <int DT, int BLOCK, int U>
 __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* __restrict__ win, int nwin,
                                                       const int32_t* __restrict__ offs,
                                                       const int64_t* __restrict__ col_ptr, Outs o, int slab_log2,
-                                                      int umax, Counters* ctr_w) {
+                                                      int umax, int only_dtype, Counters* ctr_w) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ unsigned long long red[BLOCK / 32 + 1];
   BitmapSmem sm;
@@ -269,14 +270,11 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
     const Window W = win[wi];
     const int q = inst_of(in, W.col);
     const Inst* I = in.inst + q;
+    if (only_dtype >= 0 && I->dtype != only_dtype) continue;
+    using V = typename std::conditional<DT == 1, double, float>::type;
     const int64_t out = col_ptr[W.col] - (in.col_inst ? col_ptr[I->colbase] : 0) + W.out_off;
-    int32_t* out_row = out_row_of(o, q) + out;
-    if (DT == 1 || (DT == 2 && I->dtype == 1))
-      bitmap_item<double, BLOCK, U>(in, W, I, offs, out_row, static_cast<double*>(out_val_of(o, q)) + out, sm,
-                                    slab_log2, ctr_w);
-    else
-      bitmap_item<float, BLOCK, U>(in, W, I, offs, out_row, static_cast<float*>(out_val_of(o, q)) + out, sm,
-                                   slab_log2, ctr_w);
+    bitmap_item<V, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
+                             slab_log2, ctr_w);
   }
 }
 
@@ -303,38 +301,43 @@ static size_t bitmap_smem_bytes(int slab_log2, int umax) {
 template <int DT, int BLOCK>
 static cudaError_t launch_bitmap_t(const Inputs& in, const Window* win, int n_win, const int32_t* offs,
                                    const int64_t* col_ptr, const Outs& out, int slab_log2, int umax, size_t smem,
-                                   Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+                                   int only_dtype, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
   auto kern = k_num_bitmap<DT, BLOCK, 4>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = dev.sms * blocks_per_sm(dev, smem + sizeof(unsigned long long) * (BLOCK / 32 + 1), BLOCK);
   if (grid > n_win) grid = n_win;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, BLOCK, smem, st>>>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, ctr_w);
+  kern<<<grid, BLOCK, smem, st>>>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, only_dtype, ctr_w);
   return cudaGetLastError();
 }
 
 template <int DT>
 static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_win, const int32_t* offs,
-                                    const int64_t* col_ptr, const Outs& out, int umax, Counters* ctr_w,
-                                    const DeviceInfo& dev, cudaStream_t st) {
+                                    const int64_t* col_ptr, const Outs& out, int umax, int only_dtype,
+                                    Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
   int slab_log2 = 10;
   while (slab_log2 < NUM_SLAB_LOG2_MAX && ((int64_t)1 << slab_log2) < (int64_t)in.mmax) ++slab_log2;
   const size_t smem = bitmap_smem_bytes(slab_log2, umax);
   if (smem > (size_t)dev.smem_optin) return cudaErrorInvalidConfiguration;
   // Small bitmaps leave room for several blocks per SM: use 512 threads.
   if (smem <= (size_t)dev.smem_per_sm / 2 - 2048)
-    return launch_bitmap_t<DT, 512>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, smem, ctr_w, dev, st);
-  return launch_bitmap_t<DT, 1024>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, smem, ctr_w, dev, st);
+    return launch_bitmap_t<DT, 512>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, smem, only_dtype, ctr_w,
+                                    dev, st);
+  return launch_bitmap_t<DT, 1024>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, smem, only_dtype, ctr_w,
+                                   dev, st);
 }
 
 cudaError_t launch_num_cta(const Inputs& in, int dt, const Window* win, int n_win, const int32_t* offs,
                            const int64_t* col_ptr, const Outs& out, int window_max, Counters* ctr_w,
                            const DeviceInfo& dev, cudaStream_t st) {
   if (n_win <= 0) return cudaSuccess;
-  if (dt == 0) return launch_num_cta_t<0>(in, win, n_win, offs, col_ptr, out, window_max, ctr_w, dev, st);
-  if (dt == 1) return launch_num_cta_t<1>(in, win, n_win, offs, col_ptr, out, window_max, ctr_w, dev, st);
-  return launch_num_cta_t<2>(in, win, n_win, offs, col_ptr, out, window_max, ctr_w, dev, st);
+  if (dt == 0) return launch_num_cta_t<0>(in, win, n_win, offs, col_ptr, out, window_max, -1, ctr_w, dev, st);
+  if (dt == 1) return launch_num_cta_t<1>(in, win, n_win, offs, col_ptr, out, window_max, -1, ctr_w, dev, st);
+  // Mixed batch: one launch per dtype, each skipping the other dtype's items.
+  cudaError_t e = launch_num_cta_t<0>(in, win, n_win, offs, col_ptr, out, window_max, 0, ctr_w, dev, st);
+  if (e == cudaSuccess) e = launch_num_cta_t<1>(in, win, n_win, offs, col_ptr, out, window_max, 1, ctr_w, dev, st);
+  return e;
 }
 
 }  // namespace spk

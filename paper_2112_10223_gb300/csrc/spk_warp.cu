@@ -58,6 +58,7 @@ struct WarpColArgs {
   Counters* ctr_w;
   int smax;
   int force_dedup;
+  int only_dtype;          // numeric, mixed batch: process only this dtype's columns (-1: all)
 };
 
 __device__ __forceinline__ const int32_t* shfl_ptr(const int32_t* p, int src) {
@@ -334,13 +335,13 @@ __device__ __forceinline__ int warp_column(const Inputs& in, const WarpColArgs& 
   }
 }
 
-// DT: 0 = every problem float, 1 = every problem double, 2 = per-problem
-// dtype (a mixed batch; shared memory sized for doubles).  BATCH: columns of
-// several problems (looked up per column); otherwise one problem, whose
-// inputs' pointers lanes may hold for the whole launch (resident mode).
+// DT: 0 = float values, 1 = double values (a batch mixing both runs the
+// numeric kernel once per dtype, skipping the other dtype's columns).  BATCH:
+// columns of several problems (looked up per column); otherwise one problem,
+// whose inputs' pointers lanes may hold for the whole launch (resident mode).
 template <int DT, bool NUMERIC, bool BATCH, int WARPS, int U>
 __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColArgs a) {
-  using VB = typename std::conditional<DT == 0, float, double>::type;  // value bytes per slot
+  using VB = typename std::conditional<DT == 1, double, float>::type;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int smax = a.smax;
@@ -378,7 +379,9 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColAr
     const int j = BATCH ? cur.g - I->colbase : cur.g;
     const int qb = max(5, ceil_log2(cur.s));
     const int NB = 1 << qb;
-    if (NB > smax) {  // not reachable for a warp-class column
+    if (NUMERIC && BATCH && a.only_dtype >= 0 && I->dtype != a.only_dtype) {
+      // another launch handles this column
+    } else if (NB > smax) {  // not reachable for a warp-class column
       if (lane == 0) atomicOr(&a.ctr_w->err, ERR_INTERNAL);
     } else {
       const uint32_t mul = BATCH ? __ldg(&I->bucket_mul[qb]) : s_mul[qb];
@@ -394,12 +397,8 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColAr
         const int64_t out = cur.out - (BATCH ? a.col_ptr[I->colbase] : 0);
         int32_t* orow = (BATCH ? out_row_of(a.out, cur.q) : a.out.row0) + out;
         void* oval = BATCH ? out_val_of(a.out, cur.q) : a.out.val0;
-        if (DT == 1 || (DT == 2 && I->dtype == 1))
-          warp_column<double, true, U>(in, a, sm, cur, k, off, j, mul, NB, orow, static_cast<double*>(oval) + out,
-                                       resident, my_ri, my_va, lane);
-        else
-          warp_column<float, true, U>(in, a, sm, cur, k, off, j, mul, NB, orow, static_cast<float*>(oval) + out,
-                                      resident, my_ri, my_va, lane);
+        warp_column<VB, true, U>(in, a, sm, cur, k, off, j, mul, NB, orow, static_cast<VB*>(oval) + out, resident,
+                                 my_ri, my_va, lane);
       }
     }
     __syncwarp();
@@ -431,13 +430,12 @@ static int blocks_per_sm(const DeviceInfo& dev, size_t smem_per_block, int threa
 template <int DT, bool NUMERIC>
 static cudaError_t launch_warp_col(const Inputs& in, WarpColArgs a, int warp_max, int n_cols_hint,
                                    const DeviceInfo& dev, cudaStream_t st) {
-  using VB = typename std::conditional<DT == 0, float, double>::type;
+  using VB = typename std::conditional<DT == 1, double, float>::type;
   constexpr int WARPS = 8;
   a.smax = pow2_at_least(warp_max) < 32 ? 32 : pow2_at_least(warp_max);
   const size_t smem = (size_t)WARPS * warp_col_bytes<VB, NUMERIC>(a.smax);
-  // A mixed-dtype launch is always a batch.
-  auto kern = (DT == 2 || in.col_inst) ? k_warp_col<DT, NUMERIC, true, WARPS, NUMERIC ? 8 : 16>
-                                       : k_warp_col<DT == 2 ? 1 : DT, NUMERIC, false, WARPS, NUMERIC ? 8 : 16>;
+  auto kern = in.col_inst ? k_warp_col<DT, NUMERIC, true, WARPS, NUMERIC ? 8 : 16>
+                          : k_warp_col<DT, NUMERIC, false, WARPS, NUMERIC ? 8 : 16>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = dev.sms * blocks_per_sm(dev, smem + 128, WARPS * 32);
@@ -458,6 +456,7 @@ cudaError_t launch_sym_warp(const Inputs& in, const int32_t* list, const int32_t
   a.s_arr = s;
   a.u_out = u;
   a.ctr_w = ctr_w;
+  a.only_dtype = -1;
   return launch_warp_col<0, false>(in, a, warp_max, -1, dev, st);
 }
 
@@ -475,9 +474,15 @@ cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const
   a.out = out;
   a.ctr_w = ctr_w;
   a.force_dedup = force_dedup;
+  a.only_dtype = -1;
   if (dt == 0) return launch_warp_col<0, true>(in, a, warp_max, n_cols, dev, st);
   if (dt == 1) return launch_warp_col<1, true>(in, a, warp_max, n_cols, dev, st);
-  return launch_warp_col<2, true>(in, a, warp_max, n_cols, dev, st);
+  // Mixed batch: one launch per dtype, each skipping the other dtype's columns.
+  a.only_dtype = 0;
+  cudaError_t e = launch_warp_col<0, true>(in, a, warp_max, n_cols, dev, st);
+  a.only_dtype = 1;
+  if (e == cudaSuccess) e = launch_warp_col<1, true>(in, a, warp_max, n_cols, dev, st);
+  return e;
 }
 
 }  // namespace spk
