@@ -43,7 +43,8 @@ __host__ __device__ constexpr int padded_words(int n) { return n + (n >> 4) + 1;
 template <typename V, bool NUMERIC>
 __host__ __device__ constexpr size_t warp_col_bytes(int smax) {
   return ((size_t)smax * ((NUMERIC ? sizeof(V) : 0) + sizeof(int32_t)) +
-          (size_t)padded_words(smax) * sizeof(uint32_t) + (size_t)(smax / 2 + 1) * sizeof(uint32_t) + 15) &
+          (size_t)padded_words(smax) * sizeof(uint32_t) + (size_t)(smax / 2 + 1) * sizeof(uint32_t) +
+          (NUMERIC ? 0 : (size_t)1024 * sizeof(uint32_t)) + 15) &
          ~(size_t)15;
 }
 
@@ -69,8 +70,13 @@ __device__ __forceinline__ const V* shfl_vptr(const V* p, int src) {
   return reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
 }
 
-// Calls f(row, value, valid) for every entry of the chunk (32 inputs at most),
-// lane by lane in flattened order.  Equal-length chunks map positions with one
+// Runs f on every entry of the chunk (32 inputs at most), lane by lane in
+// flattened order; e is the entry's position in that order.  Per-entry work is
+// split in two: f.pre(row, value, valid, e) issues the shared-memory atomic
+// and returns its result, f.post(result, row, value, valid, e) consumes it.
+// A round calls pre for all its U entries before any post, so the U atomics
+// are in flight together instead of each one's result stalling the next
+// (warps issue in order).  Equal-length chunks map positions with one
 // multiply-high and run their full rounds without bounds checks.
 template <bool VALS, int U, typename V, typename F>
 __device__ __forceinline__ void for_each_entry(const ChunkMap& cm, const int32_t* srow, const V* svals, int lane,
@@ -90,8 +96,11 @@ __device__ __forceinline__ void for_each_entry(const ChunkMap& cm, const int32_t
         r[t] = __ldg(shfl_ptr(srow, sg) + off);
         if constexpr (VALS) v[t] = __ldg(shfl_vptr(svals, sg) + off);
       }
+      uint32_t tok[U];
 #pragma unroll
-      for (int t = 0; t < U; ++t) f(r[t], v[t], true);
+      for (int t = 0; t < U; ++t) tok[t] = f.pre(r[t], v[t], true, e0 + t * 32 + lane);
+#pragma unroll
+      for (int t = 0; t < U; ++t) f.post(tok[t], r[t], v[t], true, e0 + t * 32 + lane);
     }
     for (int e0 = full; e0 < cm.total; e0 += 32) {
       const int e = e0 + lane;
@@ -106,7 +115,7 @@ __device__ __forceinline__ void for_each_entry(const ChunkMap& cm, const int32_t
         const V* vp = shfl_vptr(svals, sg);
         if (ok) v = __ldg(vp + off);
       }
-      f(r, v, ok);
+      f.post(f.pre(r, v, ok, e), r, v, ok, e);
     }
     return;
   }
@@ -129,10 +138,22 @@ __device__ __forceinline__ void for_each_entry(const ChunkMap& cm, const int32_t
         if (ok[t]) v[t] = __ldg(vp + off);
       }
     }
+    uint32_t tok[U];
 #pragma unroll
-    for (int t = 0; t < U; ++t) f(r[t], v[t], ok[t]);
+    for (int t = 0; t < U; ++t) tok[t] = f.pre(r[t], v[t], ok[t], e0 + t * 32 + lane);
+#pragma unroll
+    for (int t = 0; t < U; ++t) f.post(tok[t], r[t], v[t], ok[t], e0 + t * 32 + lane);
   }
 }
+
+// Adds the chunk's first flattened position to e.
+template <typename V, typename F>
+struct ChunkOffset {
+  F& f;
+  int base;
+  __device__ __forceinline__ uint32_t pre(int32_t r, V v, bool ok, int e) { return f.pre(r, v, ok, base + e); }
+  __device__ __forceinline__ void post(uint32_t t, int32_t r, V v, bool ok, int e) { f.post(t, r, v, ok, base + e); }
+};
 
 // All entries of local column j of the problem whose inputs are pointer-table
 // entries [off, off + k): chunk by chunk of 32 inputs.  Resident mode (a batch
@@ -148,6 +169,7 @@ __device__ __forceinline__ void for_each_column_entry(const Inputs& in, int k, i
     for_each_entry<VALS, U, V>(cm, my_ri + rbeg, VALS ? my_va + rbeg : my_va, lane, f);
     return;
   }
+  int base = 0;
   for (int cb = 0; cb < k; cb += 32) {
     const int i = cb + lane;
     int beg = 0, len = 0;
@@ -162,7 +184,9 @@ __device__ __forceinline__ void for_each_column_entry(const Inputs& in, int k, i
     }
     ChunkMap cm;
     cm.init(beg, len, lane, min(32, k - cb));
-    for_each_entry<VALS, U, V>(cm, ri, va, lane, f);
+    ChunkOffset<V, F> fo{f, base};
+    for_each_entry<VALS, U, V>(cm, ri, va, lane, fo);
+    base += cm.total;
   }
 }
 
@@ -201,9 +225,11 @@ template <typename V>
 struct BucketCount {  // pass 1: entries per order-preserving bucket
   uint32_t* cnt;
   uint32_t mul;
-  __device__ __forceinline__ void operator()(int32_t r, V, bool ok) {
+  __device__ __forceinline__ uint32_t pre(int32_t r, V, bool ok, int) {
     if (ok) atomicAdd(&cnt[pad16((int)bucket_hi(r, mul))], 1u);
+    return 0u;
   }
+  __device__ __forceinline__ void post(uint32_t, int32_t, V, bool, int) {}
 };
 
 template <typename V, bool NUMERIC>
@@ -212,20 +238,109 @@ struct BucketFile {  // pass 2: file the row (and value) at the bucket's next sl
   int32_t* skey;
   V* sval;
   uint32_t mul;
-  __device__ __forceinline__ void operator()(int32_t r, V v, bool ok) {
-    if (!ok) return;
+  // Numeric filing keeps each atomic next to its stores (measured faster
+  // there than issuing a round's atomics first); symbolic filing splits them.
+  __device__ __forceinline__ uint32_t pre(int32_t r, V v, bool ok, int) {
+    if (!ok) return 0u;
     const uint32_t pos = atomicAdd(&cnt[pad16((int)bucket_hi(r, mul))], 1u);
-    skey[pos] = r;
-    if constexpr (NUMERIC) sval[pos] = v;
+    if constexpr (NUMERIC) {
+      skey[pos] = r;
+      sval[pos] = v;
+    }
+    return pos;
+  }
+  __device__ __forceinline__ void post(uint32_t pos, int32_t r, V, bool ok, int) {
+    if constexpr (!NUMERIC)
+      if (ok) skey[pos] = r;
   }
 };
 
+// ---------------------------------------------------------------------------
+// Symbolic fast path: the number of repeated rows of a column of s <= 512
+// entries, without sorting.  Every entry sets one bit of a 2^15-bit filter
+// indexed by a multiplicative hash of its row; an entry that finds its bit
+// already set is "marked" (a repeated row or a hash collision; about
+// s^2 / 2^16 false collisions, i.e. 4 for s = 512).  Rows are staged in
+// shared memory with the mark in bit 31.  An entry is a repeat exactly when
+// it is marked and another entry of the same row is unmarked or earlier in
+// the staging order: in a group of g equal rows the first to set the bit is
+// the only unmarked one, unless a collision marked it too, and then the
+// earliest entry of the group is not counted; either way g - 1 entries count.
+// Only marked entries are compared, against all staged rows (one warp vote
+// each).  More marks than the list holds (MARK_MAX, less for small tables)
+// hand the column to the bucket path.
+// ---------------------------------------------------------------------------
+constexpr int FILTER_WORDS = 1024;  // 2^15 bits per warp
+constexpr int MARK_MAX = 48;
+
+__device__ __forceinline__ uint32_t filter_hash(int32_t r) { return (static_cast<uint32_t>(r) * 0x9E3779B1u) >> 17; }
+
+struct FilterMark {
+  uint32_t* filt;    // FILTER_WORDS words, zero on entry
+  int32_t* stage;    // s rows (bit 31: marked)
+  __device__ __forceinline__ uint32_t pre(int32_t r, int32_t, bool ok, int) {
+    if (!ok) return 0u;
+    const uint32_t h = filter_hash(r);
+    const uint32_t bit = 1u << (h & 31);
+    return atomicOr(&filt[h >> 5], bit) & bit;
+  }
+  __device__ __forceinline__ void post(uint32_t seen, int32_t r, int32_t, bool ok, int e) {
+    if (ok) stage[e] = seen ? (r | INT32_MIN) : r;
+  }
+};
+
+// Repeated rows of the column, or -1 when the marks overflow (then the caller
+// runs the bucket path).  Leaves the filter zero.
+template <int U>
+__device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, int off, int j, bool resident, int rbeg,
+                                                     int rlen, const int32_t* my_ri, int s, uint32_t* filt,
+                                                     int32_t* stage, uint32_t* marks, int cap, int lane) {
+  FilterMark fm{filt, stage};
+  for_each_column_entry<false, U, int32_t>(in, k, off, j, resident, rbeg, rlen, my_ri, nullptr, lane, fm);
+  __syncwarp();
+  constexpr int Q = 16;  // s <= 32 * Q
+  int32_t v[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int e = lane + 32 * q;
+    v[q] = e < s ? stage[e] : 0;
+  }
+  // List the marked entries; clear the filter for the next column.
+  int nmark = 0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int e = lane + 32 * q;
+    const bool marked = e < s && v[q] < 0;
+    const unsigned bal = __ballot_sync(SPK_FULL, marked);
+    const int pos = nmark + __popc(bal & ((1u << lane) - 1u));
+    if (marked && pos < cap) marks[pos] = (uint32_t)e;
+    nmark += __popc(bal);
+    if (e < s) filt[filter_hash(v[q] & INT32_MAX) >> 5] = 0u;
+  }
+  __syncwarp();
+  if (nmark > cap) return -1;
+  int reps = 0;
+  for (int i = 0; i < nmark; ++i) {
+    const int em = (int)marks[i];
+    const int32_t xm = stage[em] & INT32_MAX;
+    bool found = false;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int e = lane + 32 * q;
+      if (e < s && e != em && (v[q] & INT32_MAX) == xm && (v[q] >= 0 || e < em)) found = true;
+    }
+    reps += __any_sync(SPK_FULL, found) ? 1 : 0;
+  }
+  return reps;
+}
+
 // Per-warp shared buffers.
 struct WarpSmem {
-  unsigned char* vals;  // numeric values (room for smax doubles in a mixed batch)
+  unsigned char* vals;  // numeric values
   int32_t* skey;
   uint32_t* cnt;
   uint32_t* mlist;      // (start | size << 16) of multi-entry buckets
+  uint32_t* filt;       // symbolic: FILTER_WORDS-word filter, kept zero between columns
 };
 
 // One column: the three passes, the bucket sorts and (numeric) the write of
@@ -351,6 +466,11 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColAr
   sm.skey = reinterpret_cast<int32_t*>(base + (NUMERIC ? (size_t)smax * sizeof(VB) : 0));
   sm.cnt = reinterpret_cast<uint32_t*>(sm.skey + smax);
   sm.mlist = sm.cnt + padded_words(smax);
+  sm.filt = sm.mlist + (smax / 2 + 1);
+  if constexpr (!NUMERIC) {
+    for (int x = lane; x < FILTER_WORDS; x += 32) sm.filt[x] = 0u;
+    __syncwarp();
+  }
   __shared__ uint32_t s_mul[16];
   if (!BATCH && threadIdx.x < 16) s_mul[threadIdx.x] = in.inst[0].bucket_mul[threadIdx.x];
   __syncthreads();
@@ -386,8 +506,14 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColAr
     } else {
       const uint32_t mul = BATCH ? __ldg(&I->bucket_mul[qb]) : s_mul[qb];
       if constexpr (!NUMERIC) {
-        const int dups = warp_column<int32_t, false, U>(in, a, sm, cur, k, off, j, mul, NB, nullptr, nullptr,
-                                                        resident, my_ri, my_va, lane);
+        int dups = -1;
+        if (cur.s <= 512)
+          dups = warp_repeats_filtered<U>(in, k, off, j, resident, cur.beg, cur.len, my_ri, cur.s, sm.filt, sm.skey,
+                                          sm.mlist, min(MARK_MAX, smax / 2 + 1), lane);
+        __syncwarp();
+        if (dups < 0)
+          dups = warp_column<int32_t, false, U>(in, a, sm, cur, k, off, j, mul, NB, nullptr, nullptr, resident,
+                                                my_ri, my_va, lane);
         if (lane == 0) {
           a.u_out[cur.g] = cur.s - dups;
           n_unique += (dups == 0);

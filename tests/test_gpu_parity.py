@@ -314,3 +314,44 @@ def test_register_path_ragged_unaligned_segments(dtype, sort_mode):
     lens = torch.stack([a[0][1:] - a[0][:-1] for a in A])
     assert int(lens.max()) == 16 and int(lens.min()) == 0
     check_full(A, 256, dtype, options=spk.default_options(sort_mode=sort_mode))
+
+
+def _filter_hash(r):
+    return ((r * 0x9E3779B1) & 0xFFFFFFFF) >> 17
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_symbolic_filter_collisions_and_repeats(seed):
+    """Warp columns built from rows that collide in the symbolic filter's hash,
+    mixed with true repeats across inputs in every arrangement."""
+    g = torch.Generator().manual_seed(seed)
+    m = 1 << 20
+    # collision classes: several distinct rows with one hash value
+    by_hash = {}
+    while True:
+        r = int(torch.randint(0, m, (1,), generator=g))
+        by_hash.setdefault(_filter_hash(r), set()).add(r)
+        classes = [sorted(v) for v in by_hash.values() if len(v) >= 3]
+        if len(classes) >= 40:
+            break
+    k, n = 12, 300
+    cols = [[set() for _ in range(n)] for _ in range(k)]
+    for j in range(n):
+        cls = classes[j % len(classes)]
+        extra = torch.randint(0, m, (6,), generator=g).tolist()
+        pool = cls + extra
+        for i in range(k):
+            pick = torch.rand(len(pool), generator=g) < 0.45
+            cols[i][j] = {pool[t] for t in range(len(pool)) if pick[t]}
+    A = []
+    for i in range(k):
+        cp = [0]
+        rows = []
+        for j in range(n):
+            rr = sorted(cols[i][j])
+            rows += rr
+            cp.append(len(rows))
+        vals = synth.values(g, len(rows), F64, "int8", "cpu")
+        A.append((torch.tensor(cp, dtype=torch.int32), torch.tensor(rows, dtype=torch.int32), vals))
+    info, _ = check_full(A, m, F64, exact=True)
+    assert info["cols_warp"] == n
