@@ -91,37 +91,70 @@ __device__ __forceinline__ uint32_t own_word_mask(const uint32_t* summ, int w0, 
   return per == 32 ? all : (all & ((1u << per) - 1u));
 }
 
-// Calls f(row, value) for every entry of input segments [beg_i, beg_i + len_i)
-// of the item's inputs, 32 inputs per chunk; the warps of the block split each
-// chunk's flattened entries.  Equal-length chunks use the one-multiply map.
-template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename F>
-__device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, int off, SegF& seg, F& f) {
+// Runs every entry of input segments [beg_i, beg_i + len_i) of the item's
+// inputs, 32 inputs per chunk; the warps of the block split each chunk's
+// flattened entries.  Equal-length chunks use the one-multiply map.  Lane i
+// holds input i's row (and value) pointer; an entry takes its segment's
+// pointer by shuffle.  Per-entry work is fpre(row, value) -> token, issued for
+// a round's U entries before any fpost(token, row, value), so the round's
+// shared atomics are in flight together.
+__device__ __forceinline__ const int32_t* shfl_iptr(const int32_t* p, int src) {
+  return reinterpret_cast<const int32_t*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
+}
+template <typename V>
+__device__ __forceinline__ const V* shfl_vptr(const V* p, int src) {
+  return reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
+}
+
+template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename FPre, typename FPost>
+__device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, int off, SegF& seg, FPre& fpre,
+                                                     FPost& fpost) {
   constexpr int NW = BLOCK / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int cb = 0; cb < k; cb += 32) {
+  // The chunks of 32 inputs run side by side: `groups` of `per` warps, group
+  // g taking chunks g, g + groups, ... (all chunks' loads are in flight at once).
+  const int nch = (k + 31) >> 5;
+  const int groups = min(nch, NW);
+  const int per = NW / groups;
+  const int gid = wid / per, lw = wid - gid * per;
+  if (gid >= groups) return;  // (warp-uniform) spare warps
+  for (int cb = gid * 32; cb < k; cb += groups * 32) {
     const int i = cb + lane;
     int beg = 0, len = 0;
-    if (i < k) seg(i, &beg, &len);
+    const int32_t* rp = nullptr;
+    const V* vp = nullptr;
+    if (i < k) {
+      seg(i, &beg, &len);
+      rp = in.ri[off + i] + beg;
+      if constexpr (VALS) vp = static_cast<const V*>(in.val[off + i]) + beg;
+    }
     ChunkMap cm;
     cm.init(beg, len, lane, min(32, k - cb));
-    for (int e0 = wid * 32 * U; e0 < cm.total; e0 += NW * 32 * U) {
+    if (lw * 32 * U >= cm.total) continue;  // (warp-uniform) this warp has no entries in the chunk
+    for (int e0 = lw * 32 * U; e0 < cm.total; e0 += per * 32 * U) {
       int32_t r[U];
       V v[U];
 #pragma unroll
       for (int t = 0; t < U; ++t) {
         const int e = e0 + t * 32 + lane;
-        int sg;
-        const int idx = cm.locate(e, &sg);
+        int off_in;
+        const int sg = cm.seg_off(e, &off_in);
+        const int32_t* p = shfl_iptr(rp, sg & 31);
+        const V* q = nullptr;
+        if constexpr (VALS) q = shfl_vptr(vp, sg & 31);
         r[t] = -1;
         v[t] = V(0);
         if (e < cm.total) {
-          r[t] = __ldg(in.ri[off + cb + sg] + idx);
-          if constexpr (VALS) v[t] = __ldg(static_cast<const V*>(in.val[off + cb + sg]) + idx);
+          r[t] = __ldg(p + off_in);
+          if constexpr (VALS) v[t] = __ldg(q + off_in);
         }
       }
+      uint32_t tok[U];
+#pragma unroll
+      for (int t = 0; t < U; ++t) tok[t] = r[t] >= 0 ? fpre(r[t], v[t]) : 0u;
 #pragma unroll
       for (int t = 0; t < U; ++t)
-        if (r[t] >= 0) f(r[t], v[t]);
+        if (r[t] >= 0) fpost(tok[t], r[t], v[t]);
     }
   }
 }
@@ -166,14 +199,17 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
     };
     // Pass A: row bits (rows outside the slab are ignored: they cannot occur
     // for valid inputs, and shared-memory accesses stay in bounds).
-    auto setbit = [&](int32_t r, V) {
+    auto setbit = [&](int32_t r, V) -> uint32_t {
       const uint32_t rr = (uint32_t)(r - lo);
-      if (rr < width) {
-        const uint32_t w = rr >> 6;
-        if (set_row_bit(sm.bm, rr)) atomicOr(&sm.summ[w >> 5], 1u << (w & 31));
+      return (rr < width && set_row_bit(sm.bm, rr)) ? 1u : 0u;
+    };
+    auto mark_word = [&](uint32_t fresh, int32_t r, V) {
+      if (fresh) {
+        const uint32_t w = (uint32_t)(r - lo) >> 6;
+        atomicOr(&sm.summ[w >> 5], 1u << (w & 31));
       }
     };
-    block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, setbit);
+    block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, setbit, mark_word);
     __syncthreads();
     // Rank prefix: thread t owns bitmap words [t*per, t*per + per); their
     // non-empty ones are the set bits of `mine` (kept for the clear below).
@@ -203,7 +239,7 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
     __syncthreads();
     if (fits) {
       // Pass B: values at their rank.
-      auto add = [&](int32_t r, V v) {
+      auto add = [&](int32_t r, V v) -> uint32_t {
         const uint32_t rr = (uint32_t)(r - lo);
         if (rr < width) {
           const uint32_t w = rr >> 6;
@@ -212,8 +248,10 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
           const int q = (int)sm.wpre[w] + __popcll(below ? (bits << (64 - below)) : 0ull);
           if (bits && q < slab_u) atomicAdd(&acc[q], v);
         }
+        return 0u;
       };
-      block_for_each_entry<true, V, BLOCK, U>(in, k, off, seg, add);
+      auto none = [](uint32_t, int32_t, V) {};
+      block_for_each_entry<true, V, BLOCK, U>(in, k, off, seg, add, none);
       // Rows in rank order: one thread per non-empty word.
       for (int p = threadIdx.x; p < slab_ne; p += BLOCK) {
         const int w = sm.nel[p];

@@ -38,7 +38,11 @@ __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __r
     for (int p = threadIdx.x; p < T; p += BLOCK) keys[p] = -1;
     __syncthreads();
     int newc = 0;
-    for (int cb = 0; cb < k; cb += 32) {
+    const int nch = (k + 31) >> 5;
+    const int groups = min(nch, NW);
+    const int per = NW / groups;
+    const int gid = wid / per, lw = wid - gid * per;
+    for (int cb = gid * 32; gid < groups && cb < k; cb += groups * 32) {
       const int i = cb + lane;
       int beg = 0, len = 0;
       if (i < k) {
@@ -48,7 +52,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __r
       }
       SegWalk w;
       w.init(beg, len, lane);
-      for (int e0 = wid * 32 * U; e0 < w.total; e0 += NW * 32 * U) {
+      for (int e0 = lw * 32 * U; e0 < w.total; e0 += per * 32 * U) {
         int32_t r[U];
 #pragma unroll
         for (int t = 0; t < U; ++t) {
@@ -137,40 +141,55 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
       const int lo = slab * slab_rows;
       const int hi = (int)min((int64_t)m, (int64_t)lo + slab_rows);
       const uint32_t width = (uint32_t)(hi - lo);
-      for (int cb = 0; cb < k; cb += 32) {
+      // Chunks of 32 inputs side by side: `groups` of `wpg` warps.
+      const int nch = (k + 31) >> 5;
+      const int groups = min(nch, NW);
+      const int wpg = NW / groups;
+      const int gid = wid / wpg, lw = wid - gid * wpg;
+      for (int cb = gid * 32; gid < groups && cb < k; cb += groups * 32) {
         const int i = cb + lane;
         int beg = 0, len = 0;
+        const int32_t* rp = nullptr;  // this lane's input segment (its rows from beg)
         if (i < k) {
           const int32_t* cp = in.cp[off + i];
+          const int32_t* ri = in.ri[off + i];
           int b = __ldg(cp + j), e = __ldg(cp + j + 1);
           if (nslabs > 1) {
-            const int32_t* ri = in.ri[off + i];
             b = lower_bound_i32(ri, b, e, lo);
             e = lower_bound_i32(ri, b, e, hi);
           }
           beg = b;
           len = e - b;
+          rp = ri + b;
         }
         ChunkMap cm;
         cm.init(beg, len, lane, min(32, k - cb));
-        for (int e0 = wid * 32 * U; e0 < cm.total; e0 += NW * 32 * U) {
+        if (lw * 32 * U >= cm.total) continue;  // (warp-uniform) no entries for this warp
+        for (int e0 = lw * 32 * U; e0 < cm.total; e0 += wpg * 32 * U) {
           int32_t r[U];
 #pragma unroll
           for (int t = 0; t < U; ++t) {
             const int e = e0 + t * 32 + lane;
-            int sg;
-            const int idx = cm.locate(e, &sg);
+            int o;
+            const int sg = cm.seg_off(e, &o);
+            const int32_t* p = reinterpret_cast<const int32_t*>(
+                __shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(rp), sg & 31));
             r[t] = -1;
-            if (e < cm.total) r[t] = __ldg(in.ri[off + cb + sg] + idx);
+            if (e < cm.total) r[t] = __ldg(p + o);
           }
+          // All bit sets of the round first, then the summary marks they call for.
+          bool fresh[U];
 #pragma unroll
           for (int t = 0; t < U; ++t) {
             const uint32_t rr = (uint32_t)(r[t] - lo);
-            if (r[t] >= 0 && rr < width) {
-              const uint32_t w = rr >> 6;
-              if (set_row_bit(bm, rr)) atomicOr(&summ[w >> 5], 1u << (w & 31));
-            }
+            fresh[t] = r[t] >= 0 && rr < width && set_row_bit(bm, rr);
           }
+#pragma unroll
+          for (int t = 0; t < U; ++t)
+            if (fresh[t]) {
+              const uint32_t w = (uint32_t)(r[t] - lo) >> 6;
+              atomicOr(&summ[w >> 5], 1u << (w & 31));
+            }
         }
       }
       __syncthreads();
