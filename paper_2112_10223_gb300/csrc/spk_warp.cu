@@ -299,35 +299,43 @@ __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, in
   for_each_column_entry<false, U, int32_t>(in, k, off, j, resident, rbeg, rlen, my_ri, nullptr, lane, fm);
   __syncwarp();
   constexpr int Q = 16;  // s <= 32 * Q
+  // v[q] = staged row of position lane + 32q (INT32_MAX past s: no valid
+  // row equals it, since rows are below m < 2^31 - 1).
   int32_t v[Q];
+  uint32_t mine = 0u;  // bit q: position lane + 32q is marked
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int e = lane + 32 * q;
-    v[q] = e < s ? stage[e] : 0;
+    v[q] = e < s ? stage[e] : INT32_MAX;
+    if (e < s) {
+      filt[filter_hash(v[q] & INT32_MAX) >> 5] = 0u;  // clear the filter for the next column
+      if (v[q] < 0) mine |= 1u << q;
+    }
   }
-  // List the marked entries; clear the filter for the next column.
-  int nmark = 0;
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int e = lane + 32 * q;
-    const bool marked = e < s && v[q] < 0;
-    const unsigned bal = __ballot_sync(SPK_FULL, marked);
-    const int pos = nmark + __popc(bal & ((1u << lane) - 1u));
-    if (marked && pos < cap) marks[pos] = (uint32_t)e;
-    nmark += __popc(bal);
-    if (e < s) filt[filter_hash(v[q] & INT32_MAX) >> 5] = 0u;
-  }
-  __syncwarp();
+  // List the marked positions: per-lane counts, one warp scan, then each
+  // lane writes its own (few) positions.
+  const int cnt = __popc(mine);
+  const int inc = warp_incl_scan(cnt, lane);
+  const int nmark = __shfl_sync(SPK_FULL, inc, 31);
   if (nmark > cap) return -1;
+  int pos = inc - cnt;
+  for (uint32_t b = mine; b; b &= b - 1) marks[pos++] = (uint32_t)(lane + 32 * (__ffs(b) - 1));
+  __syncwarp();
   int reps = 0;
   for (int i = 0; i < nmark; ++i) {
     const int em = (int)marks[i];
     const int32_t xm = stage[em] & INT32_MAX;
-    bool found = false;
+    // Cheap screen first: does any of this lane's rows equal xm?
+    bool hit = false;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int e = lane + 32 * q;
-      if (e < s && e != em && (v[q] & INT32_MAX) == xm && (v[q] >= 0 || e < em)) found = true;
+    for (int q = 0; q < Q; ++q) hit |= (v[q] & INT32_MAX) == xm;
+    bool found = false;
+    if (hit) {  // rare: the marked entry itself, and true repeats
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int e = lane + 32 * q;
+        if ((v[q] & INT32_MAX) == xm && e != em && (v[q] >= 0 || e < em)) found = true;
+      }
     }
     reps += __any_sync(SPK_FULL, found) ? 1 : 0;
   }
