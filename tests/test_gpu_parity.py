@@ -355,3 +355,60 @@ def test_symbolic_filter_collisions_and_repeats(seed):
         A.append((torch.tensor(cp, dtype=torch.int32), torch.tensor(rows, dtype=torch.int32), vals))
     info, _ = check_full(A, m, F64, exact=True)
     assert info["cols_warp"] == n
+
+
+# ---------------------------------------------------------------------------
+# Maximum sizes.
+# ---------------------------------------------------------------------------
+def test_output_over_2pow31_nonzeros_int64_col_ptr():
+    """nnz(B) > 2^31 (int64 col_ptr_B): k = 2 ER inputs of 2^20 columns with 1030 rows each
+    (CTA class), generated on the device; sampled columns against the oracle plus invariants."""
+    dev = torch.device("cuda:0")
+    m = n = 1 << 20
+    A = synth.er(2, m, n, 1030, seed=21, dtype=F32, device=dev)
+    cp, ri, va, info = spk.spkadd(A, m, info=True)
+    torch.cuda.synchronize()
+    assert int(cp[-1]) > 2 ** 31 and info["cols_cta"] == n
+    check_global_invariants(A, (cp, ri, va), m)
+    cols, _ = sample_columns(A, 64, 8, seed=1)
+    last = torch.tensor([n - 3, n - 2, n - 1], device=dev)  # columns whose entries sit past 2^31
+    check_sampled(A, (cp, ri, va), m, torch.unique(torch.cat([cols, last])), F32)
+    del A, cp, ri, va
+    torch.cuda.empty_cache()
+
+
+def test_max_k_inputs():
+    """k = SPKADD_MAX_K = 65536 inputs (one entry each in a few columns): chunk loops over 2048
+    groups of 32 inputs, heavy columns with per-input window searches."""
+    k, m, n = 65536, 3000, 3
+    g = torch.Generator().manual_seed(5)
+    rows = torch.randint(0, m, (k,), generator=g)
+    colsel = torch.randint(0, n, (k,), generator=g)
+    A = []
+    for i in range(k):
+        cp = torch.zeros(n + 1, dtype=torch.int32)
+        cp[int(colsel[i]) + 1:] = 1
+        A.append((cp, rows[i:i + 1].to(torch.int32), torch.tensor([float((i % 15) - 7)], dtype=F64)))
+    info, _ = check_full(A, m, F64, exact=True, options=spk.default_options(window_max=1024))
+    assert info["k"] == k and info["cols_heavy"] == n
+
+
+def test_rows_near_int32_max():
+    """m = 2^31 - 2: rows at the top of the int32 range in warp, CTA and heavy columns."""
+    m = 2 ** 31 - 2
+    top = [m - 1, m - 2, m - 3, m - 1000, 2 ** 30, 0, 1, 2 ** 31 - 65]
+    g = torch.Generator().manual_seed(6)
+    k, n = 6, 3
+    A = []
+    for i in range(k):
+        cols = []
+        for j in range(n):
+            cnt = [8, 600, 5000][j]  # warp (s = 48), CTA (3,600) and heavy (30,000) columns
+            r = torch.unique(torch.cat([torch.tensor(top), torch.randint(m - 2 ** 22, m, (cnt,), generator=g)]))
+            cols.append(r[torch.randperm(r.numel(), generator=g)[:cnt]].sort().values)
+        cp = torch.zeros(n + 1, dtype=torch.int32)
+        cp[1:] = torch.cumsum(torch.tensor([c.numel() for c in cols]), 0)
+        rr = torch.cat(cols).to(torch.int32)
+        A.append((cp, rr, synth.values(g, rr.numel(), F64, "int8", "cpu")))
+    info, _ = check_full(A, m, F64, exact=True, options=spk.default_options(window_max=1024))
+    assert info["cols_warp"] == 1 and info["cols_cta"] == 1 and info["cols_heavy"] == 1
