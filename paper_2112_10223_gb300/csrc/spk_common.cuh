@@ -174,8 +174,7 @@ struct ChunkMap {
   int total;
   int L;
   int shift;        // log2(L) when L is a power of two, else -1
-  uint64_t magic;   // ceil(2^32 / L): e / L == (e * magic) >> 32 for e < 2^16, L <= 2^16
-  uint32_t magic32; // the same as a 32-bit factor: e / L == umulhi(e, magic32) (2 <= L < 2^16)
+  uint32_t magic32; // floor((2^32 - 1) / L) + 1: e / L == umulhi(e, magic32) for e < 2^16, 2 <= L < 2^16
   bool equal;
 
   __device__ __forceinline__ void init(int beg_, int len, int lane, int nvalid) {
@@ -187,8 +186,7 @@ struct ChunkMap {
       L = L0;
       total = L0 * nvalid;
       shift = (L0 & (L0 - 1)) == 0 ? __ffs(L0) - 1 : -1;
-      magic = (0xFFFFFFFFull / (uint64_t)L0) + 1ull;
-      magic32 = (uint32_t)magic;
+      magic32 = 0xFFFFFFFFu / (uint32_t)L0 + 1u;  // a 32-bit division (a 64-bit one costs far more)
     } else {
       w.init(beg_, len, lane);
       total = w.total;
@@ -198,7 +196,7 @@ struct ChunkMap {
   // segment.  Every lane must call it (it may shuffle).
   __device__ __forceinline__ int seg_off(int e, int* off) const {
     if (equal) {
-      const int sg = shift >= 0 ? (e >> shift) : (int)(((uint64_t)(uint32_t)e * magic) >> 32);
+      const int sg = shift >= 0 ? (e >> shift) : (int)__umulhi((uint32_t)e, magic32);
       *off = e - sg * L;
       return sg;
     }
@@ -210,7 +208,7 @@ struct ChunkMap {
   // Every lane must call it (it shuffles).
   __device__ __forceinline__ int locate(int e, int* seg) const {
     if (equal) {
-      const int sg = (int)(((uint64_t)(uint32_t)e * magic) >> 32);
+      const int sg = (int)__umulhi((uint32_t)e, magic32);
       const int b = __shfl_sync(SPK_FULL, beg, sg & 31);
       *seg = sg;
       return b + (e - sg * L);
