@@ -71,6 +71,20 @@ def make_inputs(w, device, seed, n_override=None):
     raise ValueError(w["family"])
 
 
+def shuffle_within_columns(A, seed):
+    """The same matrices with every input column's (row, value) pairs in random order."""
+    out = []
+    g = torch.Generator(device=A[0][0].device)
+    g.manual_seed(seed + 7919)
+    for cp, ri, va in A:
+        cpl = cp.to(torch.int64)
+        col = torch.repeat_interleave(torch.arange(cp.numel() - 1, device=cp.device), cpl[1:] - cpl[:-1])
+        key = col.to(torch.float64) + 0.5 * torch.rand(ri.numel(), generator=g, device=cp.device, dtype=torch.float64)
+        perm = torch.argsort(key)
+        out.append((cp, ri[perm].contiguous(), va[perm].contiguous()))
+    return out
+
+
 def algorithmic_bytes(k, n, nnz_in, nnz_out, vbytes):
     """Read every input once (rows, values, column pointers), write B once."""
     return nnz_in * (4 + vbytes) + k * (n + 1) * 4 + nnz_out * (4 + vbytes) + (n + 1) * 8
@@ -255,6 +269,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(dev)
     w = WORKLOADS[args.workload]
     A, m = make_inputs(w, dev, seed=args.seed + rank)
+    opts = None
+    if args.unordered:  # rows shuffled inside every input column; the library told so
+        A = shuffle_within_columns(A, args.seed + rank)
+        opts = spk.default_options(input_order=1)
     k = len(A)
     n = A[0][0].numel() - 1
     vbytes = 8 if w["dtype"] == torch.float64 else 4
@@ -263,7 +281,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
 
     def step(ev=None):
-        h = spk.spkadd_plan(A, m, stream=stream)
+        h = spk.spkadd_plan(A, m, stream=stream, options=opts)
         nnz = spk.spkadd_symbolic(h)
         cp = torch.empty(n + 1, dtype=torch.int64, device=dev)
         ri = torch.empty(nnz, dtype=torch.int32, device=dev)
@@ -281,7 +299,7 @@ def run_ours(args, world, rank, local):
     for _ in range(max(args.warmup, 1)):
         nnz_out, _ = step()
     # launches per step, from one untimed step
-    h = spk.spkadd_plan(A, m, stream=stream)
+    h = spk.spkadd_plan(A, m, stream=stream, options=opts)
     spk.spkadd_symbolic(h)
     cp0 = torch.empty(n + 1, dtype=torch.int64, device=dev)
     ri0 = torch.empty(nnz_out, dtype=torch.int32, device=dev)
@@ -352,7 +370,7 @@ def run_ours(args, world, rank, local):
                     copy_in(i + 1)
                 s_c.wait_event(ev_in[i])
                 with torch.cuda.stream(s_c):
-                    hh = spk.spkadd_plan(bufs[i % 2], m, stream=s_c)
+                    hh = spk.spkadd_plan(bufs[i % 2], m, stream=s_c, options=opts)
                     nz = spk.spkadd_symbolic(hh)
                     cp = torch.empty(n + 1, dtype=torch.int64, device=dev)
                     ri = torch.empty(nz, dtype=torch.int32, device=dev)
@@ -399,7 +417,8 @@ def run_ours(args, world, rank, local):
         "dtype": "f64" if vbytes == 8 else "f32", "data": "synthetic",
         "config": {"workload": args.workload, "k": k, "m": m, "n": n, "nnz_in": nnz_in, "nnz_out": nnz_out,
                    "cf": nnz_in / max(nnz_out, 1), "l2": "inputs exceed the 129 MB L2; no flush between steps",
-                   "parallelism": f"{world} independent instance(s), one per GPU", "seed": args.seed},
+                   "parallelism": f"{world} independent instance(s), one per GPU", "seed": args.seed,
+                   "input_order": "rows shuffled inside columns" if args.unordered else "sorted"},
         "hbm_gbs_step": step_gbs,
         "roofline": {"kernel": "k_warp_col<numeric> (spkadd_numeric)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
@@ -792,6 +811,8 @@ def main():
     ap.add_argument("--oracle-cols", type=int, default=1 << 20,
                     help="columns of the CPU oracle's sample (every (n / cols)-th column)")
     ap.add_argument("--info", action="store_true")
+    ap.add_argument("--unordered", action="store_true",
+                    help="shuffle rows inside every input column and run with input_order = 1")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--batch-mem-frac", type=float, default=0.55, help="device memory share of one wave")
     ap.add_argument("--batch-verify", type=int, default=2, help="instances per wave checked against the oracle")

@@ -113,6 +113,14 @@ typedef struct spkadd_options {
      * path of the numeric pass, even when the symbolic pass found no repeated
      * row (a test and diagnosis switch; results are the same). */
     int32_t sort_mode;
+    /* 0 = rows are strictly increasing inside every input column (the
+     * default; heavy columns are split into row windows by binary search,
+     * Sec. III-B).  1 = rows may come in any order inside a column (Table I:
+     * the hash method needs no sorted input): windows then read their whole
+     * column and keep the rows in range, validation checks ranges only, and
+     * a row repeated inside one input column is summed like a repeat across
+     * inputs.  B is sorted either way. */
+    int32_t input_order;
     /* Workspace allocator.  NULL alloc: cudaMallocAsync / cudaFreeAsync on
      * the plan's stream.  Otherwise alloc(bytes, stream, ctx) must return
      * device memory usable on `stream` (or NULL on failure) and
@@ -143,7 +151,8 @@ typedef struct spkadd_info {
 typedef struct spkadd_handle spkadd_handle;
 
 /* Fills *opt with the defaults (validate 0, warp_max 512, cta_max 4096,
- * window_max 4096, sort_mode 0, cudaMallocAsync).  No CUDA call. */
+ * window_max 4096, sort_mode 0, input_order 0, cudaMallocAsync).  No CUDA
+ * call. */
 void spkadd_default_options(spkadd_options* opt);
 
 /*

@@ -156,6 +156,7 @@ SPK_API void spkadd_default_options(spkadd_options* opt) {
   opt->cta_max = spk::CTA_MAX_LIMIT;
   opt->window_max = spk::WINDOW_MAX_LIMIT;
   opt->sort_mode = 0;
+  opt->input_order = 0;
 }
 
 SPK_API const char* spkadd_status_string(spkadd_status s) {
@@ -183,6 +184,7 @@ static spkadd_status check_options(const spkadd_options& o) {
   if (o.cta_max < o.warp_max || o.cta_max > spk::CTA_MAX_LIMIT) return SPKADD_ERR_INVALID_ARG;
   if (o.window_max < 1024 || o.window_max > spk::WINDOW_MAX_LIMIT) return SPKADD_ERR_INVALID_ARG;
   if (o.sort_mode != 0 && o.sort_mode != 1) return SPKADD_ERR_INVALID_ARG;
+  if (o.input_order != 0 && o.input_order != 1) return SPKADD_ERR_INVALID_ARG;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SPKADD_ERR_INVALID_ARG;
   return SPKADD_OK;
 }
@@ -350,6 +352,7 @@ static spkadd_status plan_problems(spkadd_handle** hp, bool batch, int count, co
   h->in.ncols = (int32_t)ncols;
   h->in.kmax = kmax;
   h->in.mmax = (int32_t)mmax;
+  h->in.sorted = o.input_order == 0 ? 1 : 0;
   if (multi) {
     ce = spk::launch_col_inst(h->in, h->d_col_inst, h->dev.sms, h->st);
     h->launches += 1;

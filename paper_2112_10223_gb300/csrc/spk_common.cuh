@@ -62,6 +62,7 @@ struct Inputs {
   int32_t ncols;            // total columns of all problems
   int32_t kmax;
   int32_t mmax;
+  int32_t sorted;           // rows strictly increasing inside every input column
 };
 
 __device__ __forceinline__ int inst_of(const Inputs& in, int g) { return in.col_inst ? __ldg(in.col_inst + g) : 0; }

@@ -189,7 +189,7 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
         b = o[0];
         e = o[1];
       }
-      if (nsl > 1) {
+      if (nsl > 1 && in.sorted) {  // unordered inputs: the whole segment, rows outside the slab skipped
         const int32_t* ri = in.ri[off + i];
         b = lower_bound_i32(ri, b, e, lo);
         e = lower_bound_i32(ri, b, e, hi);

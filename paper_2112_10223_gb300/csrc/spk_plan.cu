@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(256) k_col_inst(const Inst* __restrict__ inst,
 }
 
 // Optional input check: col_ptr[0] = 0, non-decreasing, col_ptr[n] = nnz;
-// rows in [0, m) and strictly increasing inside each column.
+// rows in [0, m), and strictly increasing inside each column unless the
+// inputs are declared unordered.
 __global__ void __launch_bounds__(256) k_validate(Inputs in, const int64_t* __restrict__ nnz, Counters* ctr) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int err = 0;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(256) k_validate(Inputs in, const int64_t* __re
       for (int64_t p = b; p < e; ++p) {
         const int32_t r = __ldg(ri + p);
         if (r < 0 || r >= m) err |= ERR_RANGE;
-        if (r <= prev) err |= ERR_UNSORTED;
+        if (in.sorted && r <= prev) err |= ERR_UNSORTED;
         prev = r;
       }
     }

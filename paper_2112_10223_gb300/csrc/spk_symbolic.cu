@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
           const int32_t* cp = in.cp[off + i];
           const int32_t* ri = in.ri[off + i];
           int b = __ldg(cp + j), e = __ldg(cp + j + 1);
-          if (nslabs > 1) {
+          if (nslabs > 1 && in.sorted) {  // unordered inputs: the whole column, rows outside the slab skipped
             b = lower_bound_i32(ri, b, e, lo);
             e = lower_bound_i32(ri, b, e, hi);
           }
@@ -211,6 +211,9 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
       const int ex = block_excl_scan<BLOCK>(loc, red, &slab_u);
       const int P = slab_u == 0 ? 0 : (slab_u + win_target - 1) / win_target;
       const bool whole = (nslabs == 1 && P == 1);
+      // Windows read per-input offsets found by binary search when the inputs
+      // are sorted; otherwise they read the whole column and keep their rows.
+      const bool searched = !whole && in.sorted;
       if (P > MAX_SLAB_WINDOWS) {  // win_target is validated on the host; guard anyway
         if (threadIdx.x == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
       } else if (P > 0) {
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
           bnd[P] = nwords;
           cval[P] = slab_u;
           s_wbase = atomicAdd(&ctr_w->n_windows, P);
-          s_sbase = whole ? -1 : atomicAdd(&ctr_w->n_search, P);
+          s_sbase = searched ? atomicAdd(&ctr_w->n_search, P) : -1;
         }
         // Window p starts after the word in which the running count first
         // reaches p * win_target.
@@ -241,16 +244,16 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
         const int col_u = s_col_u;
         for (int p = threadIdx.x; p < P; p += BLOCK) {
           const int wi = s_wbase + p;
-          if (wi < win_cap && (whole || s_sbase + p < win_cap)) {
+          if (wi < win_cap && (!searched || s_sbase + p < win_cap)) {
             Window w;
             w.col = g;
             w.r_lo = whole ? 0 : lo + 64 * bnd[p];
             w.r_hi = whole ? m : (int)min((int64_t)hi, (int64_t)lo + 64 * (int64_t)bnd[p + 1]);
             w.u = cval[p + 1] - cval[p];
             w.out_off = col_u + cval[p];
-            w.search = whole ? -1 : s_sbase + p;
+            w.search = searched ? s_sbase + p : -1;
             win[wi] = w;
-            if (!whole) search_list[s_sbase + p] = wi;
+            if (searched) search_list[s_sbase + p] = wi;
           } else {
             atomicOr(&ctr_w->err, ERR_WINDOW_CAP);
           }

@@ -412,3 +412,75 @@ def test_rows_near_int32_max():
         A.append((cp, rr, synth.values(g, rr.numel(), F64, "int8", "cpu")))
     info, _ = check_full(A, m, F64, exact=True, options=spk.default_options(window_max=1024))
     assert info["cols_warp"] == 1 and info["cols_cta"] == 1 and info["cols_heavy"] == 1
+
+
+# ---------------------------------------------------------------------------
+# Unordered input columns (option input_order = 1).
+# ---------------------------------------------------------------------------
+def _shuffle_within_columns(A, seed):
+    """Permute each input column's (row, value) pairs (pure data movement)."""
+    g = torch.Generator().manual_seed(seed)
+    out = []
+    for cp, ri, va in A:
+        cpl = cp.to(torch.int64)
+        n = cp.numel() - 1
+        col = torch.repeat_interleave(torch.arange(n), cpl[1:] - cpl[:-1])
+        key = col.to(torch.float64) + torch.rand(ri.numel(), generator=g, dtype=torch.float64) * 0.5
+        perm = torch.argsort(key)
+        out.append((cp, ri[perm], va[perm]))
+    return out
+
+
+UNORDERED = dict(input_order=1)
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_unordered_inputs_all_classes(dtype):
+    A = _shuffle_within_columns(synth.random_csc(9, 500, 200, density=0.08, seed=31, dtype=dtype,
+                                                 value_kind="int8"), 1)
+    assert any(bool((a[1][1:] < a[1][:-1]).any()) for a in A)  # really unordered
+    opt = spk.default_options(warp_max=250, cta_max=320, **UNORDERED)
+    info, _ = check_full(A, 500, dtype, exact=True, options=opt)
+    assert info["cols_warp"] > 0 and info["cols_cta"] > 0 and info["cols_heavy"] > 0, info
+
+
+def test_unordered_inputs_rmat_windows_read_whole_columns():
+    """Split heavy windows without per-input binary searches: every window reads its whole column."""
+    A = _shuffle_within_columns(synth.rmat(16, 13, 16, seed=32, dtype=F32), 2)
+    opt = spk.default_options(warp_max=32, cta_max=64, window_max=1024, **UNORDERED)
+    info, _ = check_full(A, 1 << 13, F32, options=opt)
+    assert info["windows"] > info["cols_cta"] + info["cols_heavy"] and info["windows_split"] == 0, info
+
+
+def test_unordered_inputs_two_row_slabs():
+    m = (1 << 20) + 4099
+    A = _shuffle_within_columns(synth.er(6, m, 5, 1500, seed=33, dtype=F64, value_kind="int8"), 3)
+    info, _ = check_full(A, m, F64, exact=True, options=spk.default_options(window_max=1024, **UNORDERED))
+    assert info["cols_heavy"] == 5
+
+
+def test_unordered_inputs_repeated_row_inside_one_input_is_summed():
+    """With unordered inputs a row may repeat inside one input column; it is summed like any term."""
+    cp = torch.tensor([0, 4, 7], dtype=torch.int32)
+    A = [(cp, torch.tensor([5, 2, 5, 9, 1, 1, 3], dtype=torch.int32),
+          torch.tensor([1.0, 2.0, 4.0, 8.0, 16.0, 32.0, 64.0], dtype=F64)),
+         (torch.tensor([0, 1, 2], dtype=torch.int32), torch.tensor([5, 3], dtype=torch.int32),
+          torch.tensor([128.0, 256.0], dtype=F64))]
+    cp_b, ri_b, va_b = run_gpu(A, 10, options=spk.default_options(**UNORDERED))
+    assert cp_b.tolist() == [0, 3, 5]
+    assert ri_b.tolist() == [2, 5, 9, 1, 3]
+    assert va_b.tolist() == [2.0, 133.0, 8.0, 48.0, 320.0]
+    want = oracle.add(to_np(A))
+    assert np.array_equal(ri_b.cpu().numpy(), want["row_idx"]) and np.array_equal(va_b.cpu().numpy(), want["val"])
+
+
+def test_validate_with_unordered_inputs():
+    A = _shuffle_within_columns(synth.er(3, 400, 50, 9, seed=34, dtype=F64), 4)
+    run_gpu(A, 400, options=spk.default_options(validate=1, **UNORDERED))  # accepted
+    with pytest.raises(spk.SpkaddError) as e:  # ordered mode rejects the same inputs
+        run_gpu(A, 400, options=spk.default_options(validate=1))
+    assert e.value.name == "SPKADD_ERR_UNSORTED"
+    bad = [A[0], A[1], (A[2][0], torch.where(A[2][1] == A[2][1][0], 400, A[2][1]), A[2][2])]
+    with pytest.raises(spk.SpkaddError) as e:
+        run_gpu(bad, 400, options=spk.default_options(validate=1, **UNORDERED))
+    assert e.value.name == "SPKADD_ERR_INDEX_RANGE"
