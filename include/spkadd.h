@@ -109,9 +109,14 @@ typedef struct spkadd_options {
     /* Maximum distinct rows per numeric row window of a heavy column
      * (range 1024..4096). */
     int32_t window_max;
-    /* 0 = default.  1 = warp-class columns always take the duplicate-merging
-     * path of the numeric pass, even when the symbolic pass found no repeated
-     * row (a test and diagnosis switch; results are the same). */
+    /* 0 = default: every column of B sorted by row.
+     * 1 = as 0, but warp-class columns always take the duplicate-merging
+     *     path of the numeric pass, even when the symbolic pass found no
+     *     repeated row (a test and diagnosis switch; results are the same).
+     * 2 = rows of a column of B may come in any order (Alg. 5 sorts only
+     *     when sorted output is wanted): warp-class columns without repeated
+     *     rows skip their final sort; col_ptr and each column's set of
+     *     (row, value) pairs are the same as with 0. */
     int32_t sort_mode;
     /* 0 = rows are strictly increasing inside every input column (the
      * default; heavy columns are split into row windows by binary search,

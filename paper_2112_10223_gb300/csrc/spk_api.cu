@@ -183,7 +183,7 @@ static spkadd_status check_options(const spkadd_options& o) {
   if (o.warp_max < 1 || o.warp_max > spk::WARP_MAX_LIMIT) return SPKADD_ERR_INVALID_ARG;
   if (o.cta_max < o.warp_max || o.cta_max > spk::CTA_MAX_LIMIT) return SPKADD_ERR_INVALID_ARG;
   if (o.window_max < 1024 || o.window_max > spk::WINDOW_MAX_LIMIT) return SPKADD_ERR_INVALID_ARG;
-  if (o.sort_mode != 0 && o.sort_mode != 1) return SPKADD_ERR_INVALID_ARG;
+  if (o.sort_mode < 0 || o.sort_mode > 2) return SPKADD_ERR_INVALID_ARG;
   if (o.input_order != 0 && o.input_order != 1) return SPKADD_ERR_INVALID_ARG;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SPKADD_ERR_INVALID_ARG;
   return SPKADD_OK;

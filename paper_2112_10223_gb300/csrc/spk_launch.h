@@ -46,7 +46,7 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counte
 // dt: 0 = every problem float, 1 = every problem double, 2 = mixed batch.
 cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const Counters* ctr, int n_cols,
                             const int32_t* s, const int32_t* u, const int64_t* col_ptr, const Outs& out,
-                            int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
+                            int warp_max, int sort_mode, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
 cudaError_t launch_num_cta(const Inputs& in, int dt, const Window* win, int n_win, const int32_t* offs,
                            const int64_t* col_ptr, const Outs& out, int window_max, Counters* ctr_w,
                            const DeviceInfo& dev, cudaStream_t st);

@@ -58,7 +58,8 @@ struct WarpColArgs {
   Outs out;                // numeric: where B goes
   Counters* ctr_w;
   int smax;
-  int force_dedup;
+  int force_dedup;         // numeric: sort_mode 1
+  int unsorted_out;        // numeric: sort_mode 2
   int only_dtype;          // numeric, mixed batch: process only this dtype's columns (-1: all)
 };
 
@@ -399,6 +400,8 @@ __device__ __forceinline__ int warp_column(const Inputs& in, const WarpColArgs& 
   // Sort the multi-entry buckets, one bucket per lane (insertion sort; they
   // hold 2-3 entries mostly).  Symbolic: count the repeated rows met.
   int dups = 0;
+  // Unsorted output and no repeated row: the bucket order is all that is kept.
+  if (NUMERIC && a.unsorted_out && cur.u == s) nmulti = 0;
   for (int i = lane; i < nmulti; i += 32) {
     const uint32_t w = mlist[i];
     const int lo = (int)(w & 0xffffu), hi = lo + (int)(w >> 16);
@@ -596,7 +599,7 @@ cudaError_t launch_sym_warp(const Inputs& in, const int32_t* list, const int32_t
 
 cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const Counters* ctr, int n_cols,
                             const int32_t* s, const int32_t* u, const int64_t* col_ptr, const Outs& out,
-                            int warp_max, int force_dedup, Counters* ctr_w, const DeviceInfo& dev,
+                            int warp_max, int sort_mode, Counters* ctr_w, const DeviceInfo& dev,
                             cudaStream_t st) {
   if (n_cols <= 0) return cudaSuccess;
   WarpColArgs a{};
@@ -607,7 +610,8 @@ cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const
   a.col_ptr = col_ptr;
   a.out = out;
   a.ctr_w = ctr_w;
-  a.force_dedup = force_dedup;
+  a.force_dedup = sort_mode == 1;
+  a.unsorted_out = sort_mode == 2;
   a.only_dtype = -1;
   if (dt == 0) return launch_warp_col<0, true>(in, a, warp_max, n_cols, dev, st);
   if (dt == 1) return launch_warp_col<1, true>(in, a, warp_max, n_cols, dev, st);

@@ -115,7 +115,7 @@ def test_plan_null_handle_pointer(lib):
 
 @pytest.mark.parametrize("field,value", [
     ("warp_max", 0), ("warp_max", 513), ("cta_max", 4097), ("window_max", 1000), ("window_max", 5000),
-    ("sort_mode", 2), ("input_order", 2), ("input_order", -1),
+    ("sort_mode", 3), ("sort_mode", -1), ("input_order", 2), ("input_order", -1),
 ])
 def test_plan_rejects_bad_options(lib, field, value):
     o = spk.default_options(**{field: value})

@@ -484,3 +484,33 @@ def test_validate_with_unordered_inputs():
     with pytest.raises(spk.SpkaddError) as e:
         run_gpu(bad, 400, options=spk.default_options(validate=1, **UNORDERED))
     assert e.value.name == "SPKADD_ERR_INDEX_RANGE"
+
+
+# ---------------------------------------------------------------------------
+# Unsorted output (sort_mode = 2).
+# ---------------------------------------------------------------------------
+def _sorted_columns(cp, ri, va):
+    """Each column's (row, value) pairs sorted by row (host numpy)."""
+    cp, ri, va = cp.cpu().numpy(), ri.cpu().numpy(), va.cpu().numpy()
+    order = np.concatenate([cp[j] + np.argsort(ri[cp[j]:cp[j + 1]], kind="stable") for j in range(len(cp) - 1)]
+                           or [np.zeros(0, dtype=np.int64)]).astype(np.int64)
+    return cp, ri[order], va[order]
+
+
+@pytest.mark.parametrize("dtype,kind", [(F64, "int8"), (F32, "uniform")])
+def test_unsorted_output_same_pairs(dtype, kind):
+    # m = 2^20: most columns have no repeated row, so they skip the sort
+    A = synth.er(32, 1 << 20, 700, 16, seed=41, dtype=dtype, value_kind=kind)
+    cp, ri, va = run_gpu(A, 1 << 20, options=spk.default_options(sort_mode=2))
+    unsorted = any(bool((ri[int(cp[j]) + 1:int(cp[j + 1])] < ri[int(cp[j]):int(cp[j + 1]) - 1]).any())
+                   for j in range(700))
+    assert unsorted  # the mode really leaves some columns unsorted
+    want = oracle.add(to_np(A))
+    compare(_sorted_columns(cp, ri, va), want, dtype, exact=(kind == "int8"))
+
+
+def test_unsorted_output_with_repeats_and_all_classes():
+    A = synth.random_csc(9, 300, 200, density=0.1, seed=42, dtype=F64, value_kind="int8")
+    opt = spk.default_options(sort_mode=2, warp_max=200, cta_max=300)
+    cp, ri, va = run_gpu(A, 300, options=opt)
+    compare(_sorted_columns(cp, ri, va), oracle.add(to_np(A)), F64, exact=True)
