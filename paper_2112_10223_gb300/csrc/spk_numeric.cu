@@ -106,9 +106,16 @@ __device__ __forceinline__ const V* shfl_vptr(const V* p, int src) {
   return reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
 }
 
+// A lane's segment bounds, kept from pass A for pass B when its warp walks a
+// single chunk (k <= 32 * warp groups): pass B then skips the reload.
+struct SegCache {
+  int beg, len;
+  bool valid;
+};
+
 template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename FPre, typename FPost>
 __device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, int off, SegF& seg, FPre& fpre,
-                                                     FPost& fpost) {
+                                                     FPost& fpost, SegCache& sc) {
   constexpr int NW = BLOCK / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // The chunks of 32 inputs run side by side: `groups` of `per` warps, group
@@ -124,9 +131,19 @@ __device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, in
     const int32_t* rp = nullptr;
     const V* vp = nullptr;
     if (i < k) {
-      seg(i, &beg, &len);
+      if (sc.valid) {
+        beg = sc.beg;
+        len = sc.len;
+      } else {
+        seg(i, &beg, &len);
+      }
       rp = in.ri[off + i] + beg;
       if constexpr (VALS) vp = static_cast<const V*>(in.val[off + i]) + beg;
+    }
+    if (nch <= groups) {  // this warp's only chunk: remember its bounds for the next pass
+      sc.beg = beg;
+      sc.len = len;
+      sc.valid = true;
     }
     ChunkMap cm;
     cm.init(beg, len, lane, min(32, k - cb));
@@ -209,7 +226,8 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
         atomicOr(&sm.summ[w >> 5], 1u << (w & 31));
       }
     };
-    block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, setbit, mark_word);
+    SegCache sc{0, 0, false};
+    block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, setbit, mark_word, sc);
     __syncthreads();
     // Rank prefix: thread t owns bitmap words [t*per, t*per + per); their
     // non-empty ones are the set bits of `mine` (kept for the clear below).
@@ -251,7 +269,7 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
         return 0u;
       };
       auto none = [](uint32_t, int32_t, V) {};
-      block_for_each_entry<true, V, BLOCK, U>(in, k, off, seg, add, none);
+      block_for_each_entry<true, V, BLOCK, U>(in, k, off, seg, add, none, sc);
       // Rows in rank order: one thread per non-empty word.
       for (int p = threadIdx.x; p < slab_ne; p += BLOCK) {
         const int w = sm.nel[p];
@@ -304,8 +322,12 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
   for (int x = threadIdx.x; x < sm.W64; x += BLOCK) sm.bm[x] = 0ull;
   for (int x = threadIdx.x; x < sm.NSW; x += BLOCK) sm.summ[x] = 0u;
   __syncthreads();
+  // The next item's window record is fetched while the current item runs.
+  Window Wn{};
+  if (blockIdx.x < nwin) Wn = win[blockIdx.x];
   for (int wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
-    const Window W = win[wi];
+    const Window W = Wn;
+    if (wi + (int)gridDim.x < nwin) Wn = win[wi + gridDim.x];
     const int q = inst_of(in, W.col);
     const Inst* I = in.inst + q;
     if (only_dtype >= 0 && I->dtype != only_dtype) continue;
