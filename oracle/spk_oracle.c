@@ -18,8 +18,9 @@
  *     values.
  *   - Output columns are sorted by row (the optional sort of Alg. 4 and 5,
  *     taken as required).
- *   - If an input column repeats a row (invalid input; the GPU library's
- *     validate mode rejects it) every copy is still one term of the sum.
+ *   - If an input column repeats a row (invalid when inputs are declared
+ *     sorted, allowed when they are declared unordered) every copy is still
+ *     one term of the sum.
  *
  * Method: the definition written out, nothing more.  For each requested
  * column, gather the triples (r, i, v) of all k inputs, sort them by
