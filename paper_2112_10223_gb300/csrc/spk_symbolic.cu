@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
       const int nwords = (int)((width + 63) >> 6);
       int per = 1;
       while (per * BLOCK < nwords && per < 32) per <<= 1;
+      if (per * BLOCK < nwords && threadIdx.x == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);  // host sizing prevents it
       const int w0 = threadIdx.x * per;
       uint32_t mine = 0u;
       if (w0 < nwords) {
@@ -310,14 +311,17 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counte
   while (slab_log2 < SLAB_BITS && ((int64_t)1 << slab_log2) < (int64_t)in.mmax) ++slab_log2;
   const size_t w64 = (size_t)1 << (slab_log2 - 6);
   const size_t smem = w64 * 8 + ((w64 + 31) / 32) * 4 + 16;
-  auto kern = k_sym_heavy<HEAVY_BLOCK, 4>;
+  // Small slabs: 256-thread blocks, several columns in flight per SM; a slab
+  // bitmap that fills the SM: one 1024-thread block.
+  const bool small = smem * 2 + 4096 <= (size_t)dev.smem_per_sm / 2;
+  auto kern = small ? k_sym_heavy<256, 8> : k_sym_heavy<HEAVY_BLOCK, 4>;
+  const int block = small ? 256 : HEAVY_BLOCK;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const size_t static_smem = sizeof(int) * (2 * (MAX_SLAB_WINDOWS + 1) + HEAVY_BLOCK / 32 + 4);
-  const int grid = dev.sms * blocks_per_sm(dev, smem + static_smem, HEAVY_BLOCK);
+  const size_t static_smem = sizeof(int) * (2 * (MAX_SLAB_WINDOWS + 1) + block / 32 + 4);
+  const int grid = dev.sms * blocks_per_sm(dev, smem + static_smem, block);
   // Windows end on 64-row words: a window holds at most win_target + 63 rows.
-  kern<<<grid, HEAVY_BLOCK, smem, st>>>(in, list, ctr, u, win, search_list, win_cap, window_max - 64, slab_log2,
-                                        ctr_w);
+  kern<<<grid, block, smem, st>>>(in, list, ctr, u, win, search_list, win_cap, window_max - 64, slab_log2, ctr_w);
   return cudaGetLastError();
 }
 
