@@ -411,7 +411,7 @@ SPK_API spkadd_status spkadd_batch_plan(spkadd_handle** hp, int count, const int
 static spkadd_status run_symbolic(spkadd_handle* h) {
   cudaError_t ce = cudaSuccess;
   if (h->ncols > 0) {
-    ce = spk::launch_sym_heavy(h->in, h->d_hl, h->d_ctr, h->d_u, h->d_win, h->d_search, h->win_cap, h->d_ctr,
+    ce = spk::launch_sym_heavy(h->in, h->d_hl, h->d_s, h->d_ctr, h->d_u, h->d_win, h->d_search, h->win_cap, h->d_ctr,
                                h->opt.window_max, h->dev, h->st);
     if (ce == cudaSuccess)
       ce = spk::launch_sym_cta(h->in, h->d_cl, h->d_s, h->d_ctr, h->d_u, h->d_win, h->win_cap, h->d_ctr,

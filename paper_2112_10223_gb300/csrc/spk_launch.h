@@ -39,7 +39,8 @@ cudaError_t launch_sym_warp(const Inputs& in, const int32_t* list, const int32_t
 cudaError_t launch_sym_cta(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr, int32_t* u,
                            Window* win, int64_t win_cap, Counters* ctr_w, int cta_max, const DeviceInfo& dev,
                            cudaStream_t st);
-cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counters* ctr, int32_t* u, Window* win,
+cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr, int32_t* u,
+                             Window* win,
                              int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
                              const DeviceInfo& dev, cudaStream_t st);
 

@@ -192,54 +192,30 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_apply(const int32_t* __rest
   if (blockIdx.x == 0 && threadIdx.x == 0) col_ptr[n] = *grand_total;
 }
 
-// First position p in [lo, hi) with a[p] >= key (hi if none), found by one
-// warp: each step probes 32 evenly spaced positions and keeps the gap where
-// the key falls, so the range shrinks 32-fold per dependent load instead of
-// 2-fold.  Every lane returns the result.
-__device__ __forceinline__ int warp_lower_bound(const int32_t* __restrict__ a, int lo, int hi, int32_t key,
-                                                int lane) {
-  while (hi - lo > 32) {
-    const int step = (hi - lo + 31) >> 5;  // >= 2
-    const int p = lo + lane * step;
-    const bool ge = p >= hi || __ldg(a + p) >= key;
-    const unsigned bal = __ballot_sync(SPK_FULL, ge);
-    if (bal & 1u) return lo;  // a[lo] >= key
-    const int f = bal ? __ffs(bal) - 1 : 32;  // first probe at or past the key
-    const int nlo = lo + (f - 1) * step + 1;  // probe f-1 is below the key
-    hi = f == 32 ? hi : min(hi, lo + f * step);
-    lo = nlo;
-  }
-  const int p = lo + lane;
-  const bool ge = p >= hi || __ldg(a + p) >= key;
-  const unsigned bal = __ballot_sync(SPK_FULL, ge);
-  return bal ? min(lo + __ffs(bal) - 1, hi) : hi;
-}
-
 // Per-input offsets of split row windows (Sec. III-B: "partition rows ...
 // using binary searches"): for window w and input i, the first entry of
-// A_i(:,col) with row >= r_lo and the first with row >= r_hi.  One warp per
-// (window, input) pair; rows of the offset table are kmax inputs wide.
+// A_i(:,col) with row >= r_lo and the first with row >= r_hi.  One thread per
+// (window, input) pair (measured faster than a warp-wide 32-way search per
+// pair: with thousands of pairs in flight the per-pair setup dominates);
+// rows of the offset table are kmax inputs wide.
 __global__ void __launch_bounds__(256) k_window_search(Inputs in, const Window* __restrict__ win,
                                                        const int32_t* __restrict__ search_list, int n_search,
                                                        int32_t* __restrict__ offs) {
-  const int lane = threadIdx.x & 31;
   const int64_t total = (int64_t)n_search * in.kmax;
-  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total; t += wstride) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
     const int s = (int)(t / in.kmax), i = (int)(t - (int64_t)s * in.kmax);
     const Window w = win[search_list[s]];
     const Inst* I = in.inst + inst_of(in, w.col);
-    if (i >= I->k) continue;  // (warp-uniform)
+    if (i >= I->k) continue;
     const int j = w.col - I->colbase;
     const int32_t* cp = in.cp[I->ptr_off + i];
     const int b = __ldg(cp + j), e = __ldg(cp + j + 1);
     const int32_t* ri = in.ri[I->ptr_off + i];
-    const int lo = warp_lower_bound(ri, b, e, w.r_lo, lane);
-    const int hi = warp_lower_bound(ri, lo, e, w.r_hi, lane);
-    if (lane == 0) {
-      offs[2 * t] = lo;
-      offs[2 * t + 1] = hi;
-    }
+    const int lo = lower_bound_i32(ri, b, e, w.r_lo);
+    const int hi = lower_bound_i32(ri, lo, e, w.r_hi);
+    offs[2 * t] = lo;
+    offs[2 * t + 1] = hi;
   }
 }
 
@@ -308,9 +284,9 @@ cudaError_t launch_scan(const int32_t* u, int n, long long* tile_buf, int64_t* c
 cudaError_t launch_window_search(const Inputs& in, const Window* win, const int32_t* search_list, int n_search,
                                  int32_t* offs, int sms, cudaStream_t st) {
   if (n_search <= 0) return cudaSuccess;
-  const int64_t total = (int64_t)n_search * in.kmax;  // one warp each
-  int64_t blocks = (total + 7) / 8;
-  if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+  const int64_t total = (int64_t)n_search * in.kmax;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > (int64_t)sms * 32) blocks = (int64_t)sms * 32;
   k_window_search<<<(int)blocks, 256, 0, st>>>(in, win, search_list, n_search, offs);
   return cudaGetLastError();
 }

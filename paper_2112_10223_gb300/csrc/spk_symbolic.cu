@@ -102,6 +102,8 @@ __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __r
 
 constexpr int HEAVY_BLOCK = 1024;
 constexpr int MAX_SLAB_WINDOWS = 1100;  // 2^20 rows / (1024 - 64) + 2
+constexpr int FILTER_WINDOWS = 3;       // see the window records below
+constexpr int FILTER_SEG = 64;
 
 // Heavy columns: one thread block per column.  Rows of one slab of 2^20 rows
 // at a time go into a 64-bit-word bitmap plus a summary bitmap (one bit per
@@ -111,6 +113,7 @@ constexpr int MAX_SLAB_WINDOWS = 1100;  // 2^20 rows / (1024 - 64) + 2
 // most win_target + 63 distinct rows (boundaries on 64-row words).
 template <int BLOCK, int U>
 __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* __restrict__ list,
+                                                     const int32_t* __restrict__ s_arr,
                                                      const Counters* __restrict__ ctr, int32_t* __restrict__ u_out,
                                                      Window* __restrict__ win, int32_t* __restrict__ search_list,
                                                      int64_t win_cap, int win_target, int slab_log2,
@@ -213,8 +216,13 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
       const int P = slab_u == 0 ? 0 : (slab_u + win_target - 1) / win_target;
       const bool whole = (nslabs == 1 && P == 1);
       // Windows read per-input offsets found by binary search when the inputs
-      // are sorted; otherwise they read the whole column and keep their rows.
-      const bool searched = !whole && in.sorted;
+      // are sorted, except in a column of one slab cut into at most
+      // FILTER_WINDOWS windows whose input segments are short (s_j <=
+      // FILTER_SEG * k): there every window reads the whole column and keeps
+      // its rows, since a few extra passes over short segments cost less
+      // than k binary searches per window.  Unordered inputs always do so.
+      const bool searched = !whole && in.sorted &&
+                            (nslabs > 1 || P > FILTER_WINDOWS || (int64_t)s_arr[g] > (int64_t)FILTER_SEG * k);
       if (P > MAX_SLAB_WINDOWS) {  // win_target is validated on the host; guard anyway
         if (threadIdx.x == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
       } else if (P > 0) {
@@ -304,7 +312,8 @@ cudaError_t launch_sym_cta(const Inputs& in, const int32_t* list, const int32_t*
   return cudaGetLastError();
 }
 
-cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counters* ctr, int32_t* u, Window* win,
+cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr, int32_t* u,
+                             Window* win,
                              int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
                              const DeviceInfo& dev, cudaStream_t st) {
   int slab_log2 = 10;
@@ -321,7 +330,7 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const Counte
   const size_t static_smem = sizeof(int) * (2 * (MAX_SLAB_WINDOWS + 1) + block / 32 + 4);
   const int grid = dev.sms * blocks_per_sm(dev, smem + static_smem, block);
   // Windows end on 64-row words: a window holds at most win_target + 63 rows.
-  kern<<<grid, block, smem, st>>>(in, list, ctr, u, win, search_list, win_cap, window_max - 64, slab_log2, ctr_w);
+  kern<<<grid, block, smem, st>>>(in, list, s, ctr, u, win, search_list, win_cap, window_max - 64, slab_log2, ctr_w);
   return cudaGetLastError();
 }
 

@@ -72,7 +72,7 @@ def test_batch_with_every_class_and_degenerate_problems(dtype):
     opt = spk.default_options(window_max=1024)
     _, info = _check_batch(problems, options=opt)
     assert info["cols_warp"] > 0 and info["cols_cta"] > 0 and info["cols_heavy"] > 0, info
-    assert info["windows_split"] > 0, info
+    assert info["windows"] > info["cols_cta"] + info["cols_heavy"], info  # some heavy columns cut into windows
 
 
 def test_mixed_dtypes_with_forced_classes():

@@ -63,7 +63,10 @@ def test_rmat_split_windows(dtype):
     A = synth.rmat(32, 14, 16, seed=1, dtype=dtype)
     opt = spk.default_options(warp_max=32, cta_max=64, window_max=1024)
     info, _ = check_full(A, 1 << 14, dtype, options=opt)
+    # columns cut into more than 3 windows use per-input binary searches, the
+    # others let each window read its whole column: both kinds occur here
     assert info["windows_split"] > 0, info
+    assert info["windows"] - info["windows_split"] > info["cols_cta"], info
 
 
 def test_rmat_default_thresholds():
