@@ -121,12 +121,6 @@ __device__ __forceinline__ int warp_max(int x) {
   return x;
 }
 
-__device__ __forceinline__ int warp_min(int x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(SPK_FULL, x, o));
-  return x;
-}
-
 // ---------------------------------------------------------------------------
 // Segment walker.  A warp walks the concatenation of up to 32 segments (one
 // per lane: input `base + lane`, elements [beg, beg + len) of that input).
@@ -244,28 +238,6 @@ __device__ __forceinline__ int block_excl_scan(int x, int* tmp, int* total) {
   return r;
 }
 
-template <int BLOCK>
-__device__ __forceinline__ int block_reduce_max(int x, int* tmp) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  x = warp_max(x);
-  if (lane == 0) tmp[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    int v = lane < BLOCK / 32 ? tmp[lane] : INT32_MIN;
-    v = warp_max(v);
-    if (lane == 0) tmp[BLOCK / 32] = v;
-  }
-  __syncthreads();
-  int r = tmp[BLOCK / 32];
-  __syncthreads();
-  return r;
-}
-
-template <int BLOCK>
-__device__ __forceinline__ int block_reduce_min(int x, int* tmp) {
-  return -block_reduce_max<BLOCK>(-x, tmp);
-}
-
 // Lower bound: first position p in [lo, hi) with a[p] >= key (hi if none).
 __device__ __forceinline__ int lower_bound_i32(const int32_t* __restrict__ a, int lo, int hi, int32_t key) {
   while (lo < hi) {
@@ -289,23 +261,6 @@ __device__ __forceinline__ uint32_t bucket_hi(int32_t r, uint32_t mul) {
 __device__ __forceinline__ bool set_row_bit(unsigned long long* bm, uint32_t rr) {
   uint32_t* half = reinterpret_cast<uint32_t*>(bm) + (rr >> 5);  // little-endian: bits 0-31 first
   return atomicOr(half, 1u << (rr & 31)) == 0u;
-}
-
-// Warp-wide exclusive scan of n 32-bit counters (n a multiple of 32) in place;
-// returns the total.
-__device__ __forceinline__ int warp_scan32(uint32_t* c, int n, int lane) {
-  const int per = n >> 5;
-  const int w0 = lane * per;
-  int loc = 0;
-  for (int t = 0; t < per; ++t) loc += (int)c[w0 + t];
-  const int inc = warp_incl_scan(loc, lane);
-  int run = inc - loc;
-  for (int t = 0; t < per; ++t) {
-    const int x = (int)c[w0 + t];
-    c[w0 + t] = (uint32_t)run;
-    run += x;
-  }
-  return __shfl_sync(SPK_FULL, inc, 31);
 }
 
 }  // namespace spk
