@@ -270,10 +270,11 @@ def run_ours(args, world, rank, local):
     w = WORKLOADS[args.workload]
     A, m = make_inputs(w, dev, seed=args.seed + rank)
     opts = None
-    if args.unordered or args.unsorted_output:
+    if args.unordered or args.unsorted_output or args.block_accumulator:
         if args.unordered:  # rows shuffled inside every input column; the library told so
             A = shuffle_within_columns(A, args.seed + rank)
-        opts = spk.default_options(input_order=1 if args.unordered else 0, sort_mode=2 if args.unsorted_output else 0)
+        opts = spk.default_options(input_order=1 if args.unordered else 0, sort_mode=2 if args.unsorted_output else 0,
+                                   block_accumulator=args.block_accumulator)
     k = len(A)
     n = A[0][0].numel() - 1
     vbytes = 8 if w["dtype"] == torch.float64 else 4
@@ -420,7 +421,8 @@ def run_ours(args, world, rank, local):
                    "cf": nnz_in / max(nnz_out, 1), "l2": "inputs exceed the 129 MB L2; no flush between steps",
                    "parallelism": f"{world} independent instance(s), one per GPU", "seed": args.seed,
                    "input_order": "rows shuffled inside columns" if args.unordered else "sorted",
-                   "output_order": "any order inside a column" if args.unsorted_output else "sorted"},
+                   "output_order": "any order inside a column" if args.unsorted_output else "sorted",
+                   "block_accumulator": ("automatic", "flat bitmap", "compact word table")[args.block_accumulator]},
         "hbm_gbs_step": step_gbs,
         "roofline": {"kernel": "k_warp_col<numeric> (spkadd_numeric)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
@@ -816,6 +818,8 @@ def main():
     ap.add_argument("--unordered", action="store_true",
                     help="shuffle rows inside every input column and run with input_order = 1")
     ap.add_argument("--unsorted-output", action="store_true", help="run with sort_mode = 2 (B's columns unsorted)")
+    ap.add_argument("--block-accumulator", type=int, default=0, choices=(0, 1, 2),
+                    help="thread-block items' accumulator: 0 automatic, 1 flat bitmap, 2 compact word table")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--batch-mem-frac", type=float, default=0.55, help="device memory share of one wave")
     ap.add_argument("--batch-verify", type=int, default=2, help="instances per wave checked against the oracle")

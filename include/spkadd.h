@@ -126,6 +126,14 @@ typedef struct spkadd_options {
      * a row repeated inside one input column is summed like a repeat across
      * inputs.  B is sorted either way. */
     int32_t input_order;
+    /* Accumulator of the thread-block items (CTA-class columns and windows
+     * of heavy columns), Sec. II-D's dense accumulator in two layouts; the
+     * result is the same.  0 = automatic: a flat row bitmap over the rows
+     * of the slab when it leaves room for two blocks per SM, else the
+     * compact table.  1 = always the flat bitmap.  2 = always the compact
+     * table (a summary bit per 32-row word plus a table of only the
+     * non-empty words: shared memory follows window_max, not m). */
+    int32_t block_accumulator;
     /* Workspace allocator.  NULL alloc: cudaMallocAsync / cudaFreeAsync on
      * the plan's stream.  Otherwise alloc(bytes, stream, ctx) must return
      * device memory usable on `stream` (or NULL on failure) and

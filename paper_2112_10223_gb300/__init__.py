@@ -75,6 +75,7 @@ class CSC(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int32), ("warp_max", ctypes.c_int32), ("cta_max", ctypes.c_int32),
                 ("window_max", ctypes.c_int32), ("sort_mode", ctypes.c_int32), ("input_order", ctypes.c_int32),
+                ("block_accumulator", ctypes.c_int32),
                 ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
 

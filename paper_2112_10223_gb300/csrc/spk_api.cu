@@ -157,6 +157,7 @@ SPK_API void spkadd_default_options(spkadd_options* opt) {
   opt->window_max = spk::WINDOW_MAX_LIMIT;
   opt->sort_mode = 0;
   opt->input_order = 0;
+  opt->block_accumulator = 0;
 }
 
 SPK_API const char* spkadd_status_string(spkadd_status s) {
@@ -185,6 +186,7 @@ static spkadd_status check_options(const spkadd_options& o) {
   if (o.window_max < 1024 || o.window_max > spk::WINDOW_MAX_LIMIT) return SPKADD_ERR_INVALID_ARG;
   if (o.sort_mode < 0 || o.sort_mode > 2) return SPKADD_ERR_INVALID_ARG;
   if (o.input_order != 0 && o.input_order != 1) return SPKADD_ERR_INVALID_ARG;
+  if (o.block_accumulator < 0 || o.block_accumulator > 2) return SPKADD_ERR_INVALID_ARG;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SPKADD_ERR_INVALID_ARG;
   return SPKADD_OK;
 }
@@ -492,8 +494,8 @@ static spkadd_status run_numeric(spkadd_handle* h, const spk::Outs& out) {
   const int cta_items = h->h_ctr.n_windows;
   if (cta_items > 0)
     ce = spk::launch_num_cta(h->in, h->dt_mode, h->d_win, cta_items, h->d_offs, h->d_colptr, out,
-                             h->opt.window_max > h->opt.cta_max ? h->opt.window_max : h->opt.cta_max, h->d_ctr,
-                             h->dev, h->st);
+                             h->opt.window_max > h->opt.cta_max ? h->opt.window_max : h->opt.cta_max,
+                             h->opt.block_accumulator, h->d_ctr, h->dev, h->st);
   h->launches += (cta_items > 0) * (h->dt_mode == 2 ? 2 : 1);
   if (ce == cudaSuccess && h->h_ctr.n_warp > 0)
     ce = spk::launch_num_warp(h->in, h->dt_mode, h->d_wl, h->d_ctr, h->h_ctr.n_warp, h->d_s, h->d_u, h->d_colptr,

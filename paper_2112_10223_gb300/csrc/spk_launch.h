@@ -49,8 +49,8 @@ cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const
                             const int32_t* s, const int32_t* u, const int64_t* col_ptr, const Outs& out,
                             int warp_max, int sort_mode, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
 cudaError_t launch_num_cta(const Inputs& in, int dt, const Window* win, int n_win, const int32_t* offs,
-                           const int64_t* col_ptr, const Outs& out, int window_max, Counters* ctr_w,
-                           const DeviceInfo& dev, cudaStream_t st);
+                           const int64_t* col_ptr, const Outs& out, int window_max, int accumulator,
+                           Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
 // Per-problem column pointers of B (a batch): out_cp[q][j] = col_ptr[colbase + j] - col_ptr[colbase].
 cudaError_t launch_out_colptr(const Inputs& in, const Outs& o, const int64_t* col_ptr, int sms, cudaStream_t st);
 // Per-problem nnz(B): nnz[q] = col_ptr[colbase + n] - col_ptr[colbase].

@@ -23,6 +23,7 @@
 // The bitmap covers a slab of 2^slab_log2 rows (at most 2^20): an item whose
 // rows span more is processed slab by slab, with per-input binary searches
 // for each slab's entries.
+#include <mutex>
 #include <type_traits>
 
 #include "spk_common.cuh"
@@ -70,7 +71,7 @@ struct BitmapSmem {
   uint32_t* summ;          // NSW = max(1, W64/32): one bit per bitmap word (kept zero between slabs)
   uint16_t* nel;           // umax: the non-empty words in row order
   int32_t* rows;           // umax: output rows of the slab in rank order
-  unsigned char* acc;      // umax values (room for doubles)
+  unsigned char* acc;      // umax values
   unsigned long long* red; // BLOCK/32 + 1 scan slots
   int W64, NSW, umax;
 };
@@ -303,6 +304,218 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
   if (threadIdx.x == 0 && (bad || u_done != W.u)) atomicOr(&ctr_w->err, ERR_INTERNAL);
 }
 
+// ---------------------------------------------------------------------------
+// Compact word table: the same exact-rank accumulator for items whose rows
+// span a large slab but are few (at most umax distinct rows).  The flat
+// bitmap's size follows the slab (128 KB at 2^20 rows); here only the
+// summary follows the slab (one bit per 32-row word: 4 KB at 2^20) and the
+// row bits live in a table of the non-empty words, which has at most umax
+// entries.  Shared memory drops to about a quarter, so several items are in
+// flight per SM instead of one.  One more pass over the item's entries:
+//
+//   pass A1  every entry sets its word's summary bit
+//   rank 1   popcount prefix over the summary: word w gets the compact
+//            index c(w) = prefix(w / 32) + popcount(summary bits below w);
+//            nel[c] = w lists the non-empty words in row order
+//   pass A2  every entry sets its bit in cw[c(w)]
+//   rank 2   popcount prefix over cw: wpre[c]
+//   pass B   acc[wpre[c] + popcount(cw[c] & bits below r)] += value
+//   write    words expanded to rows in rank order, values copied out
+// ---------------------------------------------------------------------------
+struct CompactSmem {
+  uint32_t* summ;  // NSW: one bit per 32-row word of the slab (kept zero between slabs)
+  uint16_t* spre;  // NSW: exclusive popcount prefix of the summary words
+  uint32_t* cw;    // umax: row bits of the non-empty words, in row order (kept zero)
+  uint16_t* wpre;  // umax: exclusive popcount prefix of cw
+  uint16_t* nel;   // umax: word index of each compact word
+  unsigned char* acc;
+  int* red;        // BLOCK/32 + 1 scan slots
+  int NSW, umax;
+};
+
+// Compact index of the non-empty 32-row word w.
+__device__ __forceinline__ int compact_index(const CompactSmem& sm, uint32_t w) {
+  const uint32_t x = w >> 5;
+  return (int)sm.spre[x] + __popc(sm.summ[x] & ((1u << (w & 31)) - 1u));
+}
+
+template <typename V, int BLOCK, int U>
+__device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, const Inst* I, const int32_t* offs,
+                                             int32_t* __restrict__ out_row, V* __restrict__ out_val,
+                                             const CompactSmem& sm, int slab_log2, Counters* ctr_w) {
+  const int k = I->k, off = I->ptr_off, j = W.col - I->colbase;
+  V* acc = reinterpret_cast<V*>(sm.acc);
+  const int64_t S = (int64_t)1 << slab_log2;
+  const int64_t span = (int64_t)W.r_hi - W.r_lo;
+  const int nsl = span <= 0 ? 0 : (int)((span + S - 1) >> slab_log2);
+  int u_done = 0;
+  bool bad = false;
+  for (int t = 0; t < nsl; ++t) {
+    const int lo = W.r_lo + (int)(t * S);
+    const int hi = (int)min((int64_t)W.r_hi, (int64_t)lo + S);
+    const uint32_t width = (uint32_t)(hi - lo);
+    auto seg = [&](int i, int* beg, int* len) {
+      int b, e;
+      if (W.search < 0) {
+        const int32_t* cp = in.cp[off + i];
+        b = __ldg(cp + j);
+        e = __ldg(cp + j + 1);
+      } else {
+        const int32_t* o = offs + ((int64_t)W.search * in.kmax + i) * 2;
+        b = o[0];
+        e = o[1];
+      }
+      if (nsl > 1 && in.sorted) {
+        const int32_t* ri = in.ri[off + i];
+        b = lower_bound_i32(ri, b, e, lo);
+        e = lower_bound_i32(ri, b, e, hi);
+      }
+      *beg = b;
+      *len = e - b;
+    };
+    auto none = [](uint32_t, int32_t, V) {};
+    // Pass A1: summary bits (a read first: dense items hit few words often).
+    auto mark = [&](int32_t r, V) -> uint32_t {
+      const uint32_t rr = (uint32_t)(r - lo);
+      if (rr < width) {
+        const uint32_t w = rr >> 5, bit = 1u << (w & 31);
+        if (!(sm.summ[w >> 5] & bit)) atomicOr(&sm.summ[w >> 5], bit);
+      }
+      return 0u;
+    };
+    SegCache sc{0, 0, false};
+    block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, mark, none, sc);
+    __syncthreads();
+    // Rank 1: thread t owns summary words [t*ps, t*ps + ps).
+    const int nwords = (int)((width + 31) >> 5);
+    const int nsw = (nwords + 31) >> 5;
+    const int ps = (nsw + BLOCK - 1) / BLOCK;
+    const int x0 = min(nsw, (int)threadIdx.x * ps), x1 = min(nsw, x0 + ps);
+    int loc = 0;
+    for (int x = x0; x < x1; ++x) loc += __popc(sm.summ[x]);
+    int ne;
+    int c = block_excl_scan<BLOCK>(loc, sm.red, &ne);
+    const bool ne_fits = ne <= sm.umax && !bad;
+    if (ne_fits) {
+      for (int x = x0; x < x1; ++x) {
+        sm.spre[x] = (uint16_t)c;
+        for (uint32_t bits = sm.summ[x]; bits; bits &= bits - 1) sm.nel[c++] = (uint16_t)(x * 32 + __ffs(bits) - 1);
+      }
+    } else {
+      bad = true;
+    }
+    __syncthreads();
+    int slab_u = 0;
+    bool fits = false;
+    if (ne_fits) {
+      // Pass A2: row bits of the compact words.
+      auto setbit = [&](int32_t r, V) -> uint32_t {
+        const uint32_t rr = (uint32_t)(r - lo);
+        if (rr < width) {
+          const int cc = compact_index(sm, rr >> 5);
+          const uint32_t bit = 1u << (rr & 31);
+          if (cc < ne && !(sm.cw[cc] & bit)) atomicOr(&sm.cw[cc], bit);
+        }
+        return 0u;
+      };
+      block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, setbit, none, sc);
+      __syncthreads();
+      // Rank 2: thread t owns compact words [t*pc, t*pc + pc).
+      const int pc = (ne + BLOCK - 1) / BLOCK;
+      const int c0 = min(ne, (int)threadIdx.x * pc), c1 = min(ne, c0 + pc);
+      int rl = 0;
+      for (int cc = c0; cc < c1; ++cc) rl += __popc(sm.cw[cc]);
+      int rank = block_excl_scan<BLOCK>(rl, sm.red, &slab_u);
+      fits = u_done + slab_u <= sm.umax;
+      if (fits) {
+        for (int cc = c0; cc < c1; ++cc) {
+          sm.wpre[cc] = (uint16_t)rank;
+          rank += __popc(sm.cw[cc]);
+        }
+        for (int q = threadIdx.x; q < slab_u; q += BLOCK) acc[q] = V(0);
+      } else {
+        bad = true;
+      }
+      __syncthreads();
+    }
+    if (fits) {
+      // Pass B: values at their rank.
+      auto add = [&](int32_t r, V v) -> uint32_t {
+        const uint32_t rr = (uint32_t)(r - lo);
+        if (rr < width) {
+          const int cc = compact_index(sm, rr >> 5);
+          if (cc < ne) {
+            const uint32_t bits = sm.cw[cc], b = rr & 31;
+            const int q = (int)sm.wpre[cc] + __popc(bits & ((1u << b) - 1u));
+            if (((bits >> b) & 1u) && q < slab_u) atomicAdd(&acc[q], v);
+          }
+        }
+        return 0u;
+      };
+      block_for_each_entry<true, V, BLOCK, U>(in, k, off, seg, add, none, sc);
+      __syncthreads();
+      // Rows straight from the words (consecutive words go to consecutive
+      // ranks), values copied out coalesced.  Ranks past the symbolic count
+      // are never written (B holds W.u rows here).
+      const int lim = min(slab_u, W.u - u_done);
+      int32_t* orow = out_row + u_done;
+      V* oval = out_val + u_done;
+      for (int cc = threadIdx.x; cc < ne; cc += BLOCK) {
+        int q = sm.wpre[cc];
+        const int rbase = lo + ((int)sm.nel[cc] << 5);
+        for (uint32_t bits = sm.cw[cc]; bits; bits &= bits - 1) {
+          if (q < lim) orow[q] = rbase + __ffs(bits) - 1;
+          ++q;
+        }
+      }
+      for (int q = threadIdx.x; q < lim; q += BLOCK) oval[q] = acc[q];
+      u_done += slab_u;
+      __syncthreads();
+    }
+    // Clear the compact words, then this thread's summary words.
+    if (ne_fits)
+      for (int cc = threadIdx.x; cc < ne; cc += BLOCK) sm.cw[cc] = 0u;
+    for (int x = x0; x < x1; ++x) sm.summ[x] = 0u;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && (bad || u_done != W.u)) atomicOr(&ctr_w->err, ERR_INTERNAL);
+}
+
+template <int DT, int BLOCK, int U>
+__global__ void __launch_bounds__(BLOCK) k_num_compact(Inputs in, const Window* __restrict__ win, int nwin,
+                                                       const int32_t* __restrict__ offs,
+                                                       const int64_t* __restrict__ col_ptr, Outs o, int slab_log2,
+                                                       int umax, int only_dtype, Counters* ctr_w) {
+  using V = typename std::conditional<DT == 1, double, float>::type;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ int red[BLOCK / 32 + 1];
+  CompactSmem sm;
+  sm.NSW = 1 << (slab_log2 - 10);
+  sm.umax = umax;
+  sm.acc = sm_raw;
+  sm.summ = reinterpret_cast<uint32_t*>(sm.acc + (size_t)umax * sizeof(V));
+  sm.cw = sm.summ + sm.NSW;
+  sm.spre = reinterpret_cast<uint16_t*>(sm.cw + umax);
+  sm.wpre = sm.spre + sm.NSW;
+  sm.nel = sm.wpre + umax;
+  sm.red = red;
+  for (int x = threadIdx.x; x < sm.NSW; x += BLOCK) sm.summ[x] = 0u;
+  for (int x = threadIdx.x; x < umax; x += BLOCK) sm.cw[x] = 0u;
+  __syncthreads();
+  Window Wn{};
+  if (blockIdx.x < nwin) Wn = win[blockIdx.x];
+  for (int wi = blockIdx.x; wi < nwin; wi += gridDim.x) {
+    const Window W = Wn;
+    if (wi + (int)gridDim.x < nwin) Wn = win[wi + gridDim.x];
+    const int q = inst_of(in, W.col);
+    const Inst* I = in.inst + q;
+    if (only_dtype >= 0 && I->dtype != only_dtype) continue;
+    const int64_t out = col_ptr[W.col] - (in.col_inst ? col_ptr[I->colbase] : 0) + W.out_off;
+    compact_item<V, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
+                              slab_log2, ctr_w);
+  }
+}
+
 // DT: 0 = float values, 1 = double values.  A batch mixing both runs the
 // kernel once per dtype; only_dtype >= 0 then skips the other dtype's items.
 template <int DT, int BLOCK, int U>
@@ -310,6 +523,7 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
                                                       const int32_t* __restrict__ offs,
                                                       const int64_t* __restrict__ col_ptr, Outs o, int slab_log2,
                                                       int umax, int only_dtype, Counters* ctr_w) {
+  using V = typename std::conditional<DT == 1, double, float>::type;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ unsigned long long red[BLOCK / 32 + 1];
   BitmapSmem sm;
@@ -318,7 +532,7 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
   sm.umax = umax;
   sm.bm = reinterpret_cast<unsigned long long*>(sm_raw);
   sm.acc = reinterpret_cast<unsigned char*>(sm.bm + sm.W64);
-  sm.wpre = reinterpret_cast<uint16_t*>(sm.acc + (size_t)umax * 8);
+  sm.wpre = reinterpret_cast<uint16_t*>(sm.acc + (size_t)umax * sizeof(V));
   sm.summ = reinterpret_cast<uint32_t*>(sm.wpre + ((sm.W64 + 1) & ~1));
   sm.rows = reinterpret_cast<int32_t*>(sm.summ + sm.NSW);
   sm.nel = reinterpret_cast<uint16_t*>(sm.rows + umax);
@@ -335,7 +549,6 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
     const int q = inst_of(in, W.col);
     const Inst* I = in.inst + q;
     if (only_dtype >= 0 && I->dtype != only_dtype) continue;
-    using V = typename std::conditional<DT == 1, double, float>::type;
     const int64_t out = col_ptr[W.col] - (in.col_inst ? col_ptr[I->colbase] : 0) + W.out_off;
     bitmap_item<V, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
                              slab_log2, ctr_w);
@@ -345,64 +558,105 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
-static int blocks_per_sm(const DeviceInfo& dev, size_t smem_per_block, int threads_per_block) {
-  const size_t reserve = 1024;
-  int b = (int)(dev.smem_per_sm / (smem_per_block + reserve));
-  int bt = 2048 / threads_per_block;
-  if (b > bt) b = bt;
-  if (b > 32) b = 32;
-  return b < 1 ? 1 : b;
+// Resident blocks per SM of a kernel at a block size and dynamic shared
+// memory size (registers, shared memory and threads all counted), or 0 on
+// error.  Cached: the query is not free.  The launch sets the kernel's
+// shared-memory limit itself (another size may have been set since).
+static int prepare_kernel(const void* fn, int block, size_t smem) {
+  struct Entry {
+    const void* fn;
+    int block;
+    size_t smem;
+    int blocks;
+  };
+  static std::mutex mu;
+  static Entry cache[64];
+  static int ncache = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < ncache; ++i)
+    if (cache[i].fn == fn && cache[i].block == block && cache[i].smem == smem) return cache[i].blocks;
+  int b = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, block, smem) != cudaSuccess) {
+    (void)cudaGetLastError();  // not sticky: leave no stale error for the next check
+    return 0;
+  }
+  if (b > 0 && ncache < 64) cache[ncache++] = Entry{fn, block, smem, b};
+  return b;
 }
 
-// Shared bytes of the bitmap kernel for a slab of 2^slab_log2 rows and umax ranks.
-static size_t bitmap_smem_bytes(int slab_log2, int umax) {
+// Shared bytes of the flat-bitmap kernel for a slab of 2^slab_log2 rows, umax ranks.
+static size_t bitmap_smem_bytes(int slab_log2, int umax, size_t vsize) {
   const size_t w64 = (size_t)1 << (slab_log2 - 6);
   const size_t nsw = (w64 + 31) / 32;
-  return w64 * 8 + (size_t)umax * 8 + ((w64 + 1) & ~(size_t)1) * 2 + nsw * 4 + (size_t)umax * 4 +
+  return w64 * 8 + (size_t)umax * vsize + ((w64 + 1) & ~(size_t)1) * 2 + nsw * 4 + (size_t)umax * 4 +
          (size_t)umax * 2 + 16;
 }
 
-template <int DT, int BLOCK, int U>
-static cudaError_t launch_bitmap_t(const Inputs& in, const Window* win, int n_win, const int32_t* offs,
-                                   const int64_t* col_ptr, const Outs& out, int slab_log2, int umax, size_t smem,
-                                   int only_dtype, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
-  auto kern = k_num_bitmap<DT, BLOCK, U>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// Shared bytes of the compact-table kernel.
+static size_t compact_smem_bytes(int slab_log2, int umax, size_t vsize) {
+  const size_t nsw = (size_t)1 << (slab_log2 - 10);
+  return (size_t)umax * vsize + nsw * 4 + (size_t)umax * 4 + nsw * 2 + (size_t)umax * 4 + 16;
+}
+
+template <typename K>
+static cudaError_t launch_items(K kern, int block, int blocks_per_sm, const Inputs& in, const Window* win, int n_win,
+                                const int32_t* offs, const int64_t* col_ptr, const Outs& out, int slab_log2, int umax,
+                                size_t smem, int only_dtype, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+  if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int grid = dev.sms * blocks_per_sm(dev, smem + sizeof(unsigned long long) * (BLOCK / 32 + 1), BLOCK);
+  int grid = dev.sms * blocks_per_sm;
   if (grid > n_win) grid = n_win;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, BLOCK, smem, st>>>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, only_dtype, ctr_w);
+  kern<<<grid, block, smem, st>>>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, only_dtype, ctr_w);
   return cudaGetLastError();
 }
 
+// accumulator: 0 = automatic, 1 = flat bitmap, 2 = compact word table.
+// Automatic takes the compact table when more of its blocks are resident per
+// SM (the flat bitmap's size follows the slab, the table's follows umax):
+// items are latency chains, so items in flight per SM decide the rate.
 template <int DT>
 static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_win, const int32_t* offs,
-                                    const int64_t* col_ptr, const Outs& out, int umax, int only_dtype,
-                                    Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+                                    const int64_t* col_ptr, const Outs& out, int umax, int accumulator,
+                                    int only_dtype, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+  constexpr size_t VS = DT == 1 ? 8 : 4;
   int slab_log2 = 10;
   while (slab_log2 < NUM_SLAB_LOG2_MAX && ((int64_t)1 << slab_log2) < (int64_t)in.mmax) ++slab_log2;
-  const size_t smem = bitmap_smem_bytes(slab_log2, umax);
-  if (smem > (size_t)dev.smem_optin) return cudaErrorInvalidConfiguration;
-  // Small bitmaps leave room for several blocks per SM: 256 threads each, so
-  // that more items are in flight per SM (measured best, with 8 entries per
-  // lane and round); a bitmap that fills the SM gets one 1024-thread block.
-  if (smem <= (size_t)dev.smem_per_sm / 2 - 2048)
-    return launch_bitmap_t<DT, 256, 8>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, smem, only_dtype, ctr_w,
-                                       dev, st);
-  return launch_bitmap_t<DT, 1024, 4>(in, win, n_win, offs, col_ptr, out, slab_log2, umax, smem, only_dtype, ctr_w,
-                                      dev, st);
+  const size_t sf = bitmap_smem_bytes(slab_log2, umax, VS), sc = compact_smem_bytes(slab_log2, umax, VS);
+  // Small bitmaps leave room for several blocks per SM: 256 threads each
+  // (measured best, with 8 entries per lane and round); a bitmap that fills
+  // the SM gets one 1024-thread block.
+  const bool small = sf <= (size_t)dev.smem_per_sm / 2 - 2048;
+  const void* kf = small ? (const void*)k_num_bitmap<DT, 256, 8> : (const void*)k_num_bitmap<DT, 1024, 4>;
+  const void* kc = (const void*)k_num_compact<DT, 256, 8>;
+  int bf = 0, bc = 0;
+  if (accumulator != 2 && sf <= (size_t)dev.smem_optin) bf = prepare_kernel(kf, small ? 256 : 1024, sf);
+  if (accumulator != 1 && sc <= (size_t)dev.smem_optin) bc = prepare_kernel(kc, 256, sc);
+  const bool compact = accumulator == 2 || (accumulator == 0 && bc > bf);
+  if (compact)
+    return launch_items(k_num_compact<DT, 256, 8>, 256, bc, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sc,
+                        only_dtype, ctr_w, dev, st);
+  if (small)
+    return launch_items(k_num_bitmap<DT, 256, 8>, 256, bf, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sf,
+                        only_dtype, ctr_w, dev, st);
+  return launch_items(k_num_bitmap<DT, 1024, 4>, 1024, bf, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sf,
+                      only_dtype, ctr_w, dev, st);
 }
 
 cudaError_t launch_num_cta(const Inputs& in, int dt, const Window* win, int n_win, const int32_t* offs,
-                           const int64_t* col_ptr, const Outs& out, int window_max, Counters* ctr_w,
+                           const int64_t* col_ptr, const Outs& out, int window_max, int accumulator, Counters* ctr_w,
                            const DeviceInfo& dev, cudaStream_t st) {
   if (n_win <= 0) return cudaSuccess;
-  if (dt == 0) return launch_num_cta_t<0>(in, win, n_win, offs, col_ptr, out, window_max, -1, ctr_w, dev, st);
-  if (dt == 1) return launch_num_cta_t<1>(in, win, n_win, offs, col_ptr, out, window_max, -1, ctr_w, dev, st);
+  if (dt == 0)
+    return launch_num_cta_t<0>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st);
+  if (dt == 1)
+    return launch_num_cta_t<1>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st);
   // Mixed batch: one launch per dtype, each skipping the other dtype's items.
-  cudaError_t e = launch_num_cta_t<0>(in, win, n_win, offs, col_ptr, out, window_max, 0, ctr_w, dev, st);
-  if (e == cudaSuccess) e = launch_num_cta_t<1>(in, win, n_win, offs, col_ptr, out, window_max, 1, ctr_w, dev, st);
+  cudaError_t e = launch_num_cta_t<0>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, 0, ctr_w, dev, st);
+  if (e == cudaSuccess)
+    e = launch_num_cta_t<1>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, 1, ctr_w, dev, st);
   return e;
 }
 

@@ -53,7 +53,8 @@ def test_status_strings_and_version(lib):
 
 def test_default_options(lib):
     o = spk.default_options()
-    assert (o.validate, o.warp_max, o.cta_max, o.window_max, o.sort_mode, o.input_order) == (0, 512, 4096, 4096, 0, 0)
+    assert (o.validate, o.warp_max, o.cta_max, o.window_max, o.sort_mode, o.input_order, o.block_accumulator) == \
+        (0, 512, 4096, 4096, 0, 0, 0)
 
 
 def _csc(m=4, n=3, nnz=0, cp=1, ri=0, va=0):
@@ -116,6 +117,7 @@ def test_plan_null_handle_pointer(lib):
 @pytest.mark.parametrize("field,value", [
     ("warp_max", 0), ("warp_max", 513), ("cta_max", 4097), ("window_max", 1000), ("window_max", 5000),
     ("sort_mode", 3), ("sort_mode", -1), ("input_order", 2), ("input_order", -1),
+    ("block_accumulator", 3), ("block_accumulator", -1),
 ])
 def test_plan_rejects_bad_options(lib, field, value):
     o = spk.default_options(**{field: value})

@@ -517,3 +517,93 @@ def test_unsorted_output_with_repeats_and_all_classes():
     opt = spk.default_options(sort_mode=2, warp_max=200, cta_max=300)
     cp, ri, va = run_gpu(A, 300, options=opt)
     compare(_sorted_columns(cp, ri, va), oracle.add(to_np(A)), F64, exact=True)
+
+
+# ---------------------------------------------------------------------------
+# Thread-block accumulators (option block_accumulator): the flat row bitmap
+# (1) and the compact word table (2) on the same inputs.
+# ---------------------------------------------------------------------------
+ACCS = [1, 2]
+
+
+@pytest.mark.parametrize("acc", ACCS)
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_accumulators_all_classes(acc, dtype):
+    A = synth.random_csc(9, 500, 200, density=0.08, seed=4, dtype=dtype)
+    opt = spk.default_options(warp_max=250, cta_max=320, block_accumulator=acc)
+    info, _ = check_full(A, 500, dtype, options=opt)
+    assert info["cols_cta"] > 0 and info["cols_heavy"] > 0, info
+
+
+@pytest.mark.parametrize("acc", ACCS)
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_accumulators_rmat_split_windows(acc, dtype):
+    """Skewed windows: dense near row 0 (full 32-row words), sparse in the tail."""
+    A = synth.rmat(32, 14, 16, seed=1, dtype=dtype)
+    opt = spk.default_options(warp_max=32, cta_max=64, window_max=1024, block_accumulator=acc)
+    info, _ = check_full(A, 1 << 14, dtype, options=opt)
+    assert info["windows_split"] > 0, info
+
+
+@pytest.mark.parametrize("acc", ACCS)
+def test_accumulators_two_row_slabs(acc):
+    """m > 2^20: items spanning two slabs run the accumulator once per slab."""
+    m = (1 << 20) + 4099
+    A = synth.er(6, m, 5, 1500, seed=3, dtype=F64, value_kind="int8")
+    info, _ = check_full(A, m, F64, exact=True, options=spk.default_options(window_max=1024, block_accumulator=acc))
+    assert info["cols_heavy"] == 5
+
+
+@pytest.mark.parametrize("acc", ACCS)
+def test_accumulators_unordered_two_row_slabs(acc):
+    m = (1 << 20) + 4099
+    A = _shuffle_within_columns(synth.er(6, m, 5, 1500, seed=33, dtype=F64, value_kind="int8"), 3)
+    opt = spk.default_options(window_max=1024, block_accumulator=acc, **UNORDERED)
+    check_full(A, m, F64, exact=True, options=opt)
+
+
+@pytest.mark.parametrize("acc", ACCS)
+def test_accumulators_dense_column(acc):
+    """A full column: every 32-row word of the item is full."""
+    m, k = 3000, 6
+    rows = torch.arange(m, dtype=torch.int32)
+    A = []
+    for i in range(k):
+        cp = torch.tensor([0, 0, m, m + 1], dtype=torch.int32)
+        ri = torch.cat([rows, torch.tensor([m - 1], dtype=torch.int32)])
+        A.append((cp, ri, synth.values(torch.Generator().manual_seed(i), m + 1, F64, "int8", "cpu")))
+    check_full(A, m, F64, exact=True, options=spk.default_options(block_accumulator=acc))
+
+
+@pytest.mark.parametrize("acc", ACCS)
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_accumulators_one_row_per_word_at_table_capacity(acc, dtype):
+    """4096 distinct rows, each alone in its 32-row word, over m = 2^20: the
+    compact table holds exactly window_max words (its capacity)."""
+    k, m, n = 4, 1 << 20, 6
+    g = torch.Generator().manual_seed(77)
+    words = [torch.randperm(m // 32, generator=g)[:4096].sort().values for _ in range(n)]
+    A = []
+    for i in range(k):
+        cps, ris = [0], []
+        for j in range(n):
+            mine = words[j][i::k] * 32 + torch.randint(0, 32, (1024,), generator=g)  # disjoint across inputs
+            ris.append(mine.to(torch.int32))
+            cps.append(cps[-1] + 1024)
+        ri = torch.cat(ris)
+        A.append((torch.tensor(cps, dtype=torch.int32), ri, synth.values(g, ri.numel(), dtype, "uniform", "cpu")))
+    info, _ = check_full(A, m, dtype, options=spk.default_options(block_accumulator=acc))
+    assert info["cols_cta"] == n and info["nnz_out"] == 4096 * n, info
+
+
+@pytest.mark.parametrize("acc", ACCS)
+def test_accumulators_mixed_dtype_batch(acc):
+    problems_cpu = [(synth.rmat(8, 12, 16, seed=90 + q, dtype=F64 if q % 2 else F32), 1 << 12) for q in range(4)]
+    problems_cpu.append((synth.er(5, (1 << 20) + 17, 4, 900, seed=95, dtype=F32), (1 << 20) + 17))
+    problems = [([tuple(t.to("cuda:0") for t in a) for a in A], m) for A, m in problems_cpu]
+    opt = spk.default_options(warp_max=64, cta_max=128, window_max=1024, block_accumulator=acc)
+    outs, info = spk.spkadd_batch(problems, options=opt, info=True)
+    torch.cuda.synchronize()
+    assert info["cols_cta"] > 0 and info["cols_heavy"] > 0, info
+    for (A, m), (cp, ri, va) in zip(problems_cpu, outs):
+        compare((cp.cpu().numpy(), ri.cpu().numpy(), va.cpu().numpy()), oracle.add(to_np(A)), A[0][2].dtype)
