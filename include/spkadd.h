@@ -126,13 +126,15 @@ typedef struct spkadd_options {
      * a row repeated inside one input column is summed like a repeat across
      * inputs.  B is sorted either way. */
     int32_t input_order;
-    /* Accumulator of the thread-block items (CTA-class columns and windows
-     * of heavy columns), Sec. II-D's dense accumulator in two layouts; the
-     * result is the same.  0 = automatic: a flat row bitmap over the rows
-     * of the slab when it leaves room for two blocks per SM, else the
-     * compact table.  1 = always the flat bitmap.  2 = always the compact
-     * table (a summary bit per 32-row word plus a table of only the
-     * non-empty words: shared memory follows window_max, not m). */
+    /* Layout of Sec. II-D's dense accumulator in the thread-block kernels
+     * (numeric CTA-class columns and heavy-column windows; heavy-column
+     * symbolic count); the result is the same.  1 = a flat row bitmap
+     * over a slab of up to 2^20 rows.  2 = a compact table: a summary bit
+     * per 32-row word plus a table of only the non-empty words, so shared
+     * memory follows window_max (numeric) or a fixed table size
+     * (symbolic: the slab is cut into sub-ranges that fit), not m.
+     * 0 = automatic: numeric items take the layout with more resident
+     * blocks per SM; the heavy symbolic count takes the flat bitmap. */
     int32_t block_accumulator;
     /* Workspace allocator.  NULL alloc: cudaMallocAsync / cudaFreeAsync on
      * the plan's stream.  Otherwise alloc(bytes, stream, ctx) must return

@@ -414,7 +414,7 @@ static spkadd_status run_symbolic(spkadd_handle* h) {
   cudaError_t ce = cudaSuccess;
   if (h->ncols > 0) {
     ce = spk::launch_sym_heavy(h->in, h->d_hl, h->d_s, h->d_ctr, h->d_u, h->d_win, h->d_search, h->win_cap, h->d_ctr,
-                               h->opt.window_max, h->dev, h->st);
+                               h->opt.window_max, h->opt.block_accumulator, h->dev, h->st);
     if (ce == cudaSuccess)
       ce = spk::launch_sym_cta(h->in, h->d_cl, h->d_s, h->d_ctr, h->d_u, h->d_win, h->win_cap, h->d_ctr,
                                h->opt.cta_max, h->dev, h->st);

@@ -263,4 +263,94 @@ __device__ __forceinline__ bool set_row_bit(unsigned long long* bm, uint32_t rr)
   return atomicOr(half, 1u << (rr & 31)) == 0u;
 }
 
+// ---------------------------------------------------------------------------
+// Thread-block entry walk (thread-block items of the symbolic and numeric
+// passes).
+// ---------------------------------------------------------------------------
+// Runs every entry of input segments [beg_i, beg_i + len_i) of the item's
+// inputs, 32 inputs per chunk; the warps of the block split each chunk's
+// flattened entries.  Equal-length chunks use the one-multiply map.  Lane i
+// holds input i's row (and value) pointer; an entry takes its segment's
+// pointer by shuffle.  Per-entry work is fpre(row, value) -> token, issued for
+// a round's U entries before any fpost(token, row, value), so the round's
+// shared atomics are in flight together.
+__device__ __forceinline__ const int32_t* shfl_iptr(const int32_t* p, int src) {
+  return reinterpret_cast<const int32_t*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
+}
+template <typename V>
+__device__ __forceinline__ const V* shfl_vptr(const V* p, int src) {
+  return reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
+}
+
+// A lane's segment bounds, kept from pass A for pass B when its warp walks a
+// single chunk (k <= 32 * warp groups): pass B then skips the reload.
+struct SegCache {
+  int beg, len;
+  bool valid;
+};
+
+template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename FPre, typename FPost>
+__device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, int off, SegF& seg, FPre& fpre,
+                                                     FPost& fpost, SegCache& sc) {
+  constexpr int NW = BLOCK / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // The chunks of 32 inputs run side by side: `groups` of `per` warps, group
+  // g taking chunks g, g + groups, ... (all chunks' loads are in flight at once).
+  const int nch = (k + 31) >> 5;
+  const int groups = min(nch, NW);
+  const int per = NW / groups;
+  const int gid = wid / per, lw = wid - gid * per;
+  if (gid >= groups) return;  // (warp-uniform) spare warps
+  for (int cb = gid * 32; cb < k; cb += groups * 32) {
+    const int i = cb + lane;
+    int beg = 0, len = 0;
+    const int32_t* rp = nullptr;
+    const V* vp = nullptr;
+    if (i < k) {
+      if (sc.valid) {
+        beg = sc.beg;
+        len = sc.len;
+      } else {
+        seg(i, &beg, &len);
+      }
+      rp = in.ri[off + i] + beg;
+      if constexpr (VALS) vp = static_cast<const V*>(in.val[off + i]) + beg;
+    }
+    if (nch <= groups) {  // this warp's only chunk: remember its bounds for the next pass
+      sc.beg = beg;
+      sc.len = len;
+      sc.valid = true;
+    }
+    ChunkMap cm;
+    cm.init(beg, len, lane, min(32, k - cb));
+    if (lw * 32 * U >= cm.total) continue;  // (warp-uniform) this warp has no entries in the chunk
+    for (int e0 = lw * 32 * U; e0 < cm.total; e0 += per * 32 * U) {
+      int32_t r[U];
+      V v[U];
+#pragma unroll
+      for (int t = 0; t < U; ++t) {
+        r[t] = -1;
+        v[t] = V(0);
+        if (e0 + t * 32 >= cm.total) continue;  // (warp-uniform) slot wholly past the chunk's end
+        const int e = e0 + t * 32 + lane;
+        int off_in;
+        const int sg = cm.seg_off(e, &off_in);
+        const int32_t* p = shfl_iptr(rp, sg & 31);
+        const V* q = nullptr;
+        if constexpr (VALS) q = shfl_vptr(vp, sg & 31);
+        if (e < cm.total) {
+          r[t] = __ldg(p + off_in);
+          if constexpr (VALS) v[t] = __ldg(q + off_in);
+        }
+      }
+      uint32_t tok[U];
+#pragma unroll
+      for (int t = 0; t < U; ++t) tok[t] = r[t] >= 0 ? fpre(r[t], v[t]) : 0u;
+#pragma unroll
+      for (int t = 0; t < U; ++t)
+        if (r[t] >= 0) fpost(tok[t], r[t], v[t]);
+    }
+  }
+}
+
 }  // namespace spk

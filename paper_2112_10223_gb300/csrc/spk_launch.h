@@ -24,6 +24,11 @@ struct DeviceInfo {
   int smem_per_sm;
 };
 
+// Resident blocks per SM of kernel `fn` at `block` threads and `smem` bytes of
+// dynamic shared memory (sets the kernel's shared-memory limit to smem; cached).
+// 0 on error.
+int resident_blocks(const void* fn, int block, size_t smem);
+
 cudaError_t launch_bin(const Inputs& in, int warp_max, int cta_max, int32_t* s, int32_t* u, int32_t* warp_list,
                        int32_t* cta_list, int32_t* heavy_list, Counters* ctr, int sms, cudaStream_t st);
 // Batch: col_inst[colbase + j] = q for every column j of every problem q.
@@ -42,7 +47,7 @@ cudaError_t launch_sym_cta(const Inputs& in, const int32_t* list, const int32_t*
 cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr, int32_t* u,
                              Window* win,
                              int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
-                             const DeviceInfo& dev, cudaStream_t st);
+                             int accumulator, const DeviceInfo& dev, cudaStream_t st);
 
 // dt: 0 = every problem float, 1 = every problem double, 2 = mixed batch.
 cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const Counters* ctr, int n_cols,

@@ -92,91 +92,6 @@ __device__ __forceinline__ uint32_t own_word_mask(const uint32_t* summ, int w0, 
   return per == 32 ? all : (all & ((1u << per) - 1u));
 }
 
-// Runs every entry of input segments [beg_i, beg_i + len_i) of the item's
-// inputs, 32 inputs per chunk; the warps of the block split each chunk's
-// flattened entries.  Equal-length chunks use the one-multiply map.  Lane i
-// holds input i's row (and value) pointer; an entry takes its segment's
-// pointer by shuffle.  Per-entry work is fpre(row, value) -> token, issued for
-// a round's U entries before any fpost(token, row, value), so the round's
-// shared atomics are in flight together.
-__device__ __forceinline__ const int32_t* shfl_iptr(const int32_t* p, int src) {
-  return reinterpret_cast<const int32_t*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
-}
-template <typename V>
-__device__ __forceinline__ const V* shfl_vptr(const V* p, int src) {
-  return reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
-}
-
-// A lane's segment bounds, kept from pass A for pass B when its warp walks a
-// single chunk (k <= 32 * warp groups): pass B then skips the reload.
-struct SegCache {
-  int beg, len;
-  bool valid;
-};
-
-template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename FPre, typename FPost>
-__device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, int off, SegF& seg, FPre& fpre,
-                                                     FPost& fpost, SegCache& sc) {
-  constexpr int NW = BLOCK / 32;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // The chunks of 32 inputs run side by side: `groups` of `per` warps, group
-  // g taking chunks g, g + groups, ... (all chunks' loads are in flight at once).
-  const int nch = (k + 31) >> 5;
-  const int groups = min(nch, NW);
-  const int per = NW / groups;
-  const int gid = wid / per, lw = wid - gid * per;
-  if (gid >= groups) return;  // (warp-uniform) spare warps
-  for (int cb = gid * 32; cb < k; cb += groups * 32) {
-    const int i = cb + lane;
-    int beg = 0, len = 0;
-    const int32_t* rp = nullptr;
-    const V* vp = nullptr;
-    if (i < k) {
-      if (sc.valid) {
-        beg = sc.beg;
-        len = sc.len;
-      } else {
-        seg(i, &beg, &len);
-      }
-      rp = in.ri[off + i] + beg;
-      if constexpr (VALS) vp = static_cast<const V*>(in.val[off + i]) + beg;
-    }
-    if (nch <= groups) {  // this warp's only chunk: remember its bounds for the next pass
-      sc.beg = beg;
-      sc.len = len;
-      sc.valid = true;
-    }
-    ChunkMap cm;
-    cm.init(beg, len, lane, min(32, k - cb));
-    if (lw * 32 * U >= cm.total) continue;  // (warp-uniform) this warp has no entries in the chunk
-    for (int e0 = lw * 32 * U; e0 < cm.total; e0 += per * 32 * U) {
-      int32_t r[U];
-      V v[U];
-#pragma unroll
-      for (int t = 0; t < U; ++t) {
-        const int e = e0 + t * 32 + lane;
-        int off_in;
-        const int sg = cm.seg_off(e, &off_in);
-        const int32_t* p = shfl_iptr(rp, sg & 31);
-        const V* q = nullptr;
-        if constexpr (VALS) q = shfl_vptr(vp, sg & 31);
-        r[t] = -1;
-        v[t] = V(0);
-        if (e < cm.total) {
-          r[t] = __ldg(p + off_in);
-          if constexpr (VALS) v[t] = __ldg(q + off_in);
-        }
-      }
-      uint32_t tok[U];
-#pragma unroll
-      for (int t = 0; t < U; ++t) tok[t] = r[t] >= 0 ? fpre(r[t], v[t]) : 0u;
-#pragma unroll
-      for (int t = 0; t < U; ++t)
-        if (r[t] >= 0) fpost(tok[t], r[t], v[t]);
-    }
-  }
-}
-
 // One item (a CTA-class column or a heavy column's row window [r_lo, r_hi),
 // Alg. 8: B(r1:r2, j) <- HashAdd(A_1(r1:r2, j), ..., A_k(r1:r2, j))).
 template <typename V, int BLOCK, int U>
@@ -562,7 +477,7 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
 // memory size (registers, shared memory and threads all counted), or 0 on
 // error.  Cached: the query is not free.  The launch sets the kernel's
 // shared-memory limit itself (another size may have been set since).
-static int prepare_kernel(const void* fn, int block, size_t smem) {
+int resident_blocks(const void* fn, int block, size_t smem) {
   struct Entry {
     const void* fn;
     int block;
@@ -632,8 +547,8 @@ static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_w
   const void* kf = small ? (const void*)k_num_bitmap<DT, 256, 8> : (const void*)k_num_bitmap<DT, 1024, 4>;
   const void* kc = (const void*)k_num_compact<DT, 256, 8>;
   int bf = 0, bc = 0;
-  if (accumulator != 2 && sf <= (size_t)dev.smem_optin) bf = prepare_kernel(kf, small ? 256 : 1024, sf);
-  if (accumulator != 1 && sc <= (size_t)dev.smem_optin) bc = prepare_kernel(kc, 256, sc);
+  if (accumulator != 2 && sf <= (size_t)dev.smem_optin) bf = resident_blocks(kf, small ? 256 : 1024, sf);
+  if (accumulator != 1 && sc <= (size_t)dev.smem_optin) bc = resident_blocks(kc, 256, sc);
   const bool compact = accumulator == 2 || (accumulator == 0 && bc > bf);
   if (compact)
     return launch_items(k_num_compact<DT, 256, 8>, 256, bc, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sc,

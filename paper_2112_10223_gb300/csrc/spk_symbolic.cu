@@ -56,10 +56,11 @@ __global__ void __launch_bounds__(BLOCK) k_sym_cta(Inputs in, const int32_t* __r
         int32_t r[U];
 #pragma unroll
         for (int t = 0; t < U; ++t) {
+          r[t] = -1;
+          if (e0 + t * 32 >= w.total) continue;  // (warp-uniform) slot wholly past the chunk's end
           const int e = e0 + t * 32 + lane;
           const int seg = w.find(e);
           const int idx = w.index_in_input(e, seg);
-          r[t] = -1;
           if (e < w.total) r[t] = __ldg(in.ri[off + cb + seg] + idx);
         }
 #pragma unroll
@@ -172,12 +173,13 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
           int32_t r[U];
 #pragma unroll
           for (int t = 0; t < U; ++t) {
+            r[t] = -1;
+            if (e0 + t * 32 >= cm.total) continue;  // (warp-uniform) slot wholly past the chunk's end
             const int e = e0 + t * 32 + lane;
             int o;
             const int sg = cm.seg_off(e, &o);
             const int32_t* p = reinterpret_cast<const int32_t*>(
                 __shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(rp), sg & 31));
-            r[t] = -1;
             if (e < cm.total) r[t] = __ldg(p + o);
           }
           // All bit sets of the round first, then the summary marks they call for.
@@ -280,6 +282,211 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* _
   }
 }
 
+// Heavy columns, compact form: the same count and window cuts from a summary
+// bit per 32-row word and a table of at most `cap` non-empty words, instead of
+// a bitmap over the whole slab (128 KB at 2^20 rows), so that several columns
+// are in flight per SM.  Per slab:
+//
+//   pass A1  every entry sets its word's summary bit
+//   rank 1   popcount prefix over the summary words; the slab is cut into
+//            sub-ranges of whole summary words holding at most `cap`
+//            non-empty words each (one sub-range unless the column is huge)
+//   per sub-range:
+//     pass A2  every entry of the sub-range sets its row bit in the table
+//              (sorted inputs: the sub-range's slice found by binary search)
+//     rank 2   popcount prefix over the table: distinct rows, and the window
+//              cuts where the running count reaches multiples of win_target
+//              (on 32-row words: a window holds at most win_target + 31 rows)
+template <int BLOCK, int U>
+__global__ void __launch_bounds__(BLOCK) k_sym_heavy_compact(Inputs in, const int32_t* __restrict__ list,
+                                                             const int32_t* __restrict__ s_arr,
+                                                             const Counters* __restrict__ ctr,
+                                                             int32_t* __restrict__ u_out, Window* __restrict__ win,
+                                                             int32_t* __restrict__ search_list, int64_t win_cap,
+                                                             int win_target, int slab_log2, int cap,
+                                                             Counters* ctr_w) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ int red[BLOCK / 32 + 1];
+  __shared__ int bnd[MAX_SLAB_WINDOWS + 1];
+  __shared__ int cval[MAX_SLAB_WINDOWS + 1];
+  __shared__ int s_col_u, s_wbase, s_sbase;
+  const int NSW = 1 << (slab_log2 - 10);
+  uint32_t* summ = reinterpret_cast<uint32_t*>(sm_raw);     // NSW: one bit per 32-row word (kept zero)
+  uint32_t* cw = summ + NSW;                                // cap: row bits of non-empty words (kept zero)
+  int32_t* spre = reinterpret_cast<int32_t*>(cw + cap);     // NSW: exclusive prefix of non-empty words
+  int32_t* srs = spre + NSW;                                // NSW: first summary word of each sub-range
+  for (int x = threadIdx.x; x < NSW; x += BLOCK) summ[x] = 0u;
+  for (int x = threadIdx.x; x < cap; x += BLOCK) cw[x] = 0u;
+  __syncthreads();
+  const int ncols = ctr->n_heavy;
+  const int slab_rows = 1 << slab_log2;
+  const int capw = cap - 32;  // a sub-range starts below capw words: it ends below cap
+  for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
+    const int g = list[c];
+    const Inst* I = in.inst + inst_of(in, g);
+    const int k = I->k, off = I->ptr_off, m = I->m, j = g - I->colbase;
+    const int nslabs = (int)(((int64_t)m + slab_rows - 1) / slab_rows);
+    if (threadIdx.x == 0) s_col_u = 0;
+    for (int slab = 0; slab < nslabs; ++slab) {
+      const int lo = slab * slab_rows;
+      const int hi = (int)min((int64_t)m, (int64_t)lo + slab_rows);
+      const uint32_t width = (uint32_t)(hi - lo);
+      // The column's entries of input i in rows [a, b) of this slab.
+      auto seg_rows = [&](int i, int a, int b, int* beg, int* len) {
+        const int32_t* cp = in.cp[off + i];
+        int x = __ldg(cp + j), y = __ldg(cp + j + 1);
+        if (in.sorted && (a > 0 || b < m)) {  // unordered inputs: all entries, rows outside skipped
+          const int32_t* ri = in.ri[off + i];
+          x = lower_bound_i32(ri, x, y, a);
+          y = lower_bound_i32(ri, x, y, b);
+        }
+        *beg = x;
+        *len = y - x;
+      };
+      auto seg_slab = [&](int i, int* beg, int* len) { seg_rows(i, nslabs > 1 ? lo : 0, nslabs > 1 ? hi : m, beg, len); };
+      auto none = [](uint32_t, int32_t, float) {};
+      auto mark = [&](int32_t r, float) -> uint32_t {
+        const uint32_t rr = (uint32_t)(r - lo);
+        if (rr < width) {
+          const uint32_t w = rr >> 5, bit = 1u << (w & 31);
+          if (!(summ[w >> 5] & bit)) atomicOr(&summ[w >> 5], bit);
+        }
+        return 0u;
+      };
+      SegCache sc{0, 0, false};
+      block_for_each_entry<false, float, BLOCK, U>(in, k, off, seg_slab, mark, none, sc);
+      __syncthreads();
+      // Rank 1: thread t owns summary words [x0, x1).
+      const int nwords = (int)((width + 31) >> 5);
+      const int nsw = (nwords + 31) >> 5;
+      const int ps = (nsw + BLOCK - 1) / BLOCK;
+      const int x0 = min(nsw, (int)threadIdx.x * ps), x1 = min(nsw, x0 + ps);
+      int loc = 0;
+      for (int x = x0; x < x1; ++x) loc += __popc(summ[x]);
+      int ne;
+      int run = block_excl_scan<BLOCK>(loc, red, &ne);
+      {
+        int prev_sub = x0 > 0 ? (run - __popc(summ[x0 - 1])) / capw : -1;  // sub-range of word x0 - 1
+        for (int x = x0; x < x1; ++x) {
+          const int sub = run / capw;
+          if (sub != prev_sub) srs[sub] = x;  // the prefix grows by <= 32 <= capw per word: no sub-range skipped
+          prev_sub = sub;
+          spre[x] = run;
+          run += __popc(summ[x]);
+        }
+      }
+      __syncthreads();
+      const int R = spre[nsw - 1] / capw + 1;
+      int slab_run = 0;
+      for (int sub = 0; sub < R; ++sub) {
+        const int xa = srs[sub], xb = sub + 1 < R ? srs[sub + 1] : nsw;
+        const int cbase = spre[xa];
+        const int nsub = (xb < nsw ? spre[xb] : ne) - cbase;
+        if (nsub > cap) {  // cannot happen (see capw); never index past the table
+          if (threadIdx.x == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
+          continue;
+        }
+        // Pass A2: row bits of the sub-range's non-empty words.
+        auto setbit = [&](int32_t r, float) -> uint32_t {
+          const uint32_t rr = (uint32_t)(r - lo);
+          if (rr < width) {
+            const uint32_t w = rr >> 5;
+            const int x = (int)(w >> 5);
+            if (x >= xa && x < xb) {
+              const int cc = spre[x] + __popc(summ[x] & ((1u << (w & 31)) - 1u)) - cbase;
+              const uint32_t bit = 1u << (rr & 31);
+              if (cc < nsub && !(cw[cc] & bit)) atomicOr(&cw[cc], bit);  // cc < nsub: pass A1 set w's bit
+            }
+          }
+          return 0u;
+        };
+        if (R == 1) {
+          block_for_each_entry<false, float, BLOCK, U>(in, k, off, seg_slab, setbit, none, sc);
+        } else {
+          const int ra = lo + xa * 1024, rb = (int)min((int64_t)hi, (int64_t)lo + (int64_t)xb * 1024);
+          auto seg_sub = [&](int i, int* beg, int* len) { seg_rows(i, ra, rb, beg, len); };
+          SegCache sc2{0, 0, false};
+          block_for_each_entry<false, float, BLOCK, U>(in, k, off, seg_sub, setbit, none, sc2);
+        }
+        __syncthreads();
+        // Rank 2, by summary word: thread t owns summary words [y0, y1) of the sub-range.
+        const int nx = xb - xa;
+        const int ps2 = (nx + BLOCK - 1) / BLOCK;
+        const int y0 = xa + min(nx, (int)threadIdx.x * ps2), y1 = xa + min(nx, (int)threadIdx.x * ps2 + ps2);
+        int l2 = 0;
+        for (int x = y0; x < y1; ++x) {
+          int cc = spre[x] - cbase;
+          for (int t = __popc(summ[x]); t > 0; --t) l2 += __popc(cw[cc++]);
+        }
+        int sub_u;
+        int run2 = slab_run + block_excl_scan<BLOCK>(l2, red, &sub_u);
+        // Window p starts after the word in which the running count first reaches p * win_target.
+        for (int x = y0; x < y1; ++x) {
+          int cc = spre[x] - cbase;
+          for (uint32_t bits = summ[x]; bits; bits &= bits - 1) {
+            const int wd = x * 32 + __ffs(bits) - 1;
+            const int before = run2;
+            run2 += __popc(cw[cc++]);
+            const int pb = before / win_target, pa = run2 / win_target;
+            if (pa > pb && pa >= 1 && pa <= MAX_SLAB_WINDOWS - 1) {
+              bnd[pa] = wd + 1;
+              cval[pa] = run2;
+            }
+          }
+        }
+        __syncthreads();
+        for (int cc = threadIdx.x; cc < nsub; cc += BLOCK) cw[cc] = 0u;
+        slab_run += sub_u;
+        __syncthreads();
+      }
+      const int slab_u = slab_run;
+      const int P = slab_u == 0 ? 0 : (slab_u + win_target - 1) / win_target;
+      const bool whole = (nslabs == 1 && P == 1);
+      // As in the bitmap form: split windows of sorted inputs are searched
+      // unless the column has one slab, at most FILTER_WINDOWS windows and
+      // short segments.
+      const bool searched = !whole && in.sorted &&
+                            (nslabs > 1 || P > FILTER_WINDOWS || (int64_t)s_arr[g] > (int64_t)FILTER_SEG * k);
+      if (P > MAX_SLAB_WINDOWS) {
+        if (threadIdx.x == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);
+      } else if (P > 0) {
+        if (threadIdx.x == 0) {
+          bnd[0] = 0;
+          cval[0] = 0;
+          bnd[P] = nwords;
+          cval[P] = slab_u;
+          s_wbase = atomicAdd(&ctr_w->n_windows, P);
+          s_sbase = searched ? atomicAdd(&ctr_w->n_search, P) : -1;
+        }
+        __syncthreads();
+        const int col_u = s_col_u;
+        for (int p = threadIdx.x; p < P; p += BLOCK) {
+          const int wi = s_wbase + p;
+          if (wi < win_cap && (!searched || s_sbase + p < win_cap)) {
+            Window w;
+            w.col = g;
+            w.r_lo = whole ? 0 : lo + 32 * bnd[p];
+            w.r_hi = whole ? m : (int)min((int64_t)hi, (int64_t)lo + 32 * (int64_t)bnd[p + 1]);
+            w.u = cval[p + 1] - cval[p];
+            w.out_off = col_u + cval[p];
+            w.search = searched ? s_sbase + p : -1;
+            win[wi] = w;
+            if (searched) search_list[s_sbase + p] = wi;
+          } else {
+            atomicOr(&ctr_w->err, ERR_WINDOW_CAP);
+          }
+        }
+      }
+      for (int x = x0; x < x1; ++x) summ[x] = 0u;
+      __syncthreads();
+      if (threadIdx.x == 0) s_col_u += slab_u;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) u_out[g] = s_col_u;
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
@@ -312,25 +519,48 @@ cudaError_t launch_sym_cta(const Inputs& in, const int32_t* list, const int32_t*
   return cudaGetLastError();
 }
 
+constexpr int HEAVY_CAP = 4096;  // non-empty 32-row words per sub-range of the compact form
+
+// accumulator: 0 or 1 = slab bitmap, 2 = compact table.  Unlike the numeric
+// items, the automatic choice keeps the slab bitmap even when it holds the
+// SM: a heavy column has thousands of entries or more, enough for a
+// 1024-thread block, and the largest R-MAT columns (10^5 distinct rows and
+// more) need dozens of compact sub-ranges, each with 2k binary searches on
+// the one block that owns the column (measured: R-MAT k=64 scale 20, heavy
+// symbolic 7.2 ms as a bitmap, about 13 ms compact).
 cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const int32_t* s, const Counters* ctr, int32_t* u,
-                             Window* win,
-                             int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
-                             const DeviceInfo& dev, cudaStream_t st) {
+                             Window* win, int32_t* search_list, int64_t win_cap, Counters* ctr_w, int window_max,
+                             int accumulator, const DeviceInfo& dev, cudaStream_t st) {
   int slab_log2 = 10;
   while (slab_log2 < SLAB_BITS && ((int64_t)1 << slab_log2) < (int64_t)in.mmax) ++slab_log2;
   const size_t w64 = (size_t)1 << (slab_log2 - 6);
   const size_t smem = w64 * 8 + ((w64 + 31) / 32) * 4 + 16;
+  const size_t nsw = (size_t)1 << (slab_log2 - 10);
+  const size_t smem_c = nsw * 4 + (size_t)HEAVY_CAP * 4 + nsw * 8 + 16;
   // Small slabs: 256-thread blocks, several columns in flight per SM; a slab
   // bitmap that fills the SM: one 1024-thread block.
   const bool small = smem * 2 + 4096 <= (size_t)dev.smem_per_sm / 2;
   auto kern = small ? k_sym_heavy<256, 8> : k_sym_heavy<HEAVY_BLOCK, 4>;
+  auto kern_c = k_sym_heavy_compact<256, 8>;
   const int block = small ? 256 : HEAVY_BLOCK;
+  int bf = 0, bc = 0;
+  if (accumulator != 2 && smem <= (size_t)dev.smem_optin) bf = resident_blocks((const void*)kern, block, smem);
+  if (accumulator == 2) bc = resident_blocks((const void*)kern_c, 256, smem_c);
+  if (accumulator == 2) {
+    if (bc < 1) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(kern_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
+    if (e != cudaSuccess) return e;
+    // Windows end on 32-row words: a window holds at most win_target + 31 rows.
+    kern_c<<<dev.sms * bc, 256, smem_c, st>>>(in, list, s, ctr, u, win, search_list, win_cap, window_max - 64,
+                                             slab_log2, HEAVY_CAP, ctr_w);
+    return cudaGetLastError();
+  }
+  if (bf < 1) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const size_t static_smem = sizeof(int) * (2 * (MAX_SLAB_WINDOWS + 1) + block / 32 + 4);
-  const int grid = dev.sms * blocks_per_sm(dev, smem + static_smem, block);
   // Windows end on 64-row words: a window holds at most win_target + 63 rows.
-  kern<<<grid, block, smem, st>>>(in, list, s, ctr, u, win, search_list, win_cap, window_max - 64, slab_log2, ctr_w);
+  kern<<<dev.sms * bf, block, smem, st>>>(in, list, s, ctr, u, win, search_list, win_cap, window_max - 64, slab_log2,
+                                          ctr_w);
   return cudaGetLastError();
 }
 

@@ -63,14 +63,6 @@ struct WarpColArgs {
   int only_dtype;          // numeric, mixed batch: process only this dtype's columns (-1: all)
 };
 
-__device__ __forceinline__ const int32_t* shfl_ptr(const int32_t* p, int src) {
-  return reinterpret_cast<const int32_t*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
-}
-template <typename V>
-__device__ __forceinline__ const V* shfl_vptr(const V* p, int src) {
-  return reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
-}
-
 // Runs f on every entry of the chunk (32 inputs at most), lane by lane in
 // flattened order; e is the entry's position in that order.  Per-entry work is
 // split in two: f.pre(row, value, valid, e) issues the shared-memory atomic
@@ -94,7 +86,7 @@ __device__ __forceinline__ void for_each_entry(const ChunkMap& cm, const int32_t
         const int e = e0 + t * 32 + lane;
         const int sg = (int)__umulhi((uint32_t)e, M);
         const int off = e - sg * L;
-        r[t] = __ldg(shfl_ptr(srow, sg) + off);
+        r[t] = __ldg(shfl_iptr(srow, sg) + off);
         if constexpr (VALS) v[t] = __ldg(shfl_vptr(svals, sg) + off);
       }
       uint32_t tok[U];
@@ -108,7 +100,7 @@ __device__ __forceinline__ void for_each_entry(const ChunkMap& cm, const int32_t
       const bool ok = e < cm.total;
       const int sg = ok ? (int)__umulhi((uint32_t)e, M) : 0;
       const int off = e - sg * L;
-      const int32_t* rp = shfl_ptr(srow, sg);
+      const int32_t* rp = shfl_iptr(srow, sg);
       int32_t r = -1;
       V v = V(0);
       if (ok) r = __ldg(rp + off);
@@ -128,14 +120,15 @@ __device__ __forceinline__ void for_each_entry(const ChunkMap& cm, const int32_t
     for (int t = 0; t < U; ++t) {
       const int e = e0 + t * 32 + lane;
       ok[t] = e < cm.total;
+      r[t] = -1;
+      if constexpr (VALS) v[t] = V(0);
+      if (e0 + t * 32 >= cm.total) continue;  // (warp-uniform) slot wholly past the chunk's end
       const int sg = cm.w.find(e);
       const int off = e - __shfl_sync(SPK_FULL, cm.w.P, sg);
-      const int32_t* rp = shfl_ptr(srow, sg);
-      r[t] = -1;
+      const int32_t* rp = shfl_iptr(srow, sg);
       if (ok[t]) r[t] = __ldg(rp + off);
       if constexpr (VALS) {
         const V* vp = shfl_vptr(svals, sg);
-        v[t] = V(0);
         if (ok[t]) v[t] = __ldg(vp + off);
       }
     }

@@ -607,3 +607,25 @@ def test_accumulators_mixed_dtype_batch(acc):
     assert info["cols_cta"] > 0 and info["cols_heavy"] > 0, info
     for (A, m), (cp, ri, va) in zip(problems_cpu, outs):
         compare((cp.cpu().numpy(), ri.cpu().numpy(), va.cpu().numpy()), oracle.add(to_np(A)), A[0][2].dtype)
+
+
+@pytest.mark.parametrize("acc", ACCS)
+@pytest.mark.parametrize("order", ["sorted", "unordered"])
+def test_accumulators_heavy_column_many_subranges(acc, order):
+    """A heavy column with ~32K distinct rows over 2^20 rows (its compact
+    symbolic form cuts the slab into several sub-ranges) next to a dense one
+    (every row of [0, 40000): full 32-row words, one sub-range)."""
+    k, m = 8, 1 << 20
+    g = torch.Generator().manual_seed(78)
+    A = []
+    for i in range(k):
+        sparse = torch.randperm(m, generator=g)[:4000].sort().values
+        dense = torch.arange(i * 5000, i * 5000 + 5000)  # rows [0, 40000) over the 8 inputs
+        ri = torch.cat([sparse, dense]).to(torch.int32)
+        cp = torch.tensor([0, 4000, 9000], dtype=torch.int32)
+        A.append((cp, ri, synth.values(g, ri.numel(), F64, "int8", "cpu")))
+    if order == "unordered":
+        A = _shuffle_within_columns(A, 5)
+    opt = spk.default_options(window_max=1024, block_accumulator=acc, input_order=1 if order == "unordered" else 0)
+    info, _ = check_full(A, m, F64, exact=True, options=opt)
+    assert info["cols_heavy"] == 2 and info["windows"] > 60, info
