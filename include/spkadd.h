@@ -94,8 +94,10 @@ typedef struct spkadd_options {
     /* Nonzero: spkadd_plan checks every input on the device (one extra read
      * of all row indices, then one stream synchronisation) and returns
      * SPKADD_ERR_UNSORTED / SPKADD_ERR_INDEX_RANGE on bad input.  Zero: the
-     * inputs are trusted.  Then rows outside [0, m) or out of order give an
-     * unspecified B (shared-memory accesses stay in bounds), but col_ptr
+     * inputs are trusted.  Then a row outside [0, m) in a column with
+     * s_j <= warp_max is still caught (spkadd_symbolic returns
+     * SPKADD_ERR_INDEX_RANGE); one in a larger column, or rows out of order,
+     * give an unspecified B (shared-memory accesses stay in bounds); col_ptr
      * values outside [0, nnz] make the kernels read outside row_idx/val. */
     int32_t validate;
     /* Columns whose summed input count s_j = sum_i nnz(A_i(:,j)) is at most

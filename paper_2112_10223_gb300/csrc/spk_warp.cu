@@ -153,10 +153,18 @@ struct ChunkOffset {
 // entries [off, off + k): chunk by chunk of 32 inputs.  Resident mode (a batch
 // of one with k <= 32): the lane's input pointers and (beg, len) come from
 // the caller.
+// A lane's segment bounds in the first two chunks of a non-resident column,
+// kept from the first pass over the column for the next (which then skips
+// the chain of pointer-table and column-pointer loads).
+struct ChunkCache {
+  int beg[2], len[2];
+  bool valid;
+};
+
 template <bool VALS, int U, typename V, typename F>
 __device__ __forceinline__ void for_each_column_entry(const Inputs& in, int k, int off, int j, bool resident,
                                                       int rbeg, int rlen, const int32_t* my_ri, const V* my_va,
-                                                      int lane, F& f) {
+                                                      int lane, F& f, ChunkCache& cc) {
   if (resident) {
     ChunkMap cm;
     cm.init(rbeg, rlen, lane, k);
@@ -166,15 +174,28 @@ __device__ __forceinline__ void for_each_column_entry(const Inputs& in, int k, i
   int base = 0;
   for (int cb = 0; cb < k; cb += 32) {
     const int i = cb + lane;
+    const int ci = cb >> 5;
     int beg = 0, len = 0;
     const int32_t* ri = nullptr;
     const V* va = nullptr;
     if (i < k) {
-      const int32_t* cp = in.cp[off + i];
-      beg = __ldg(cp + j);
-      len = __ldg(cp + j + 1) - beg;
+      if (ci < 2 && cc.valid) {
+        beg = cc.beg[ci];
+        len = cc.len[ci];
+      } else {
+        const int32_t* cp = in.cp[off + i];
+        beg = __ldg(cp + j);
+        len = __ldg(cp + j + 1) - beg;
+      }
       ri = in.ri[off + i] + beg;
       if constexpr (VALS) va = static_cast<const V*>(in.val[off + i]) + beg;
+    }
+    if (ci == 0) {
+      cc.beg[0] = beg;
+      cc.len[0] = len;
+    } else if (ci == 1) {
+      cc.beg[1] = beg;
+      cc.len[1] = len;
     }
     ChunkMap cm;
     cm.init(beg, len, lane, min(32, k - cb));
@@ -182,6 +203,7 @@ __device__ __forceinline__ void for_each_column_entry(const Inputs& in, int k, i
     for_each_entry<VALS, U, V>(cm, ri, va, lane, fo);
     base += cm.total;
   }
+  cc.valid = true;
 }
 
 // Scalars of one warp-class column, loaded one column ahead of their use.
@@ -283,20 +305,25 @@ struct FilterMark {
   }
 };
 
-// Repeated rows of the column, or -1 when the marks overflow (then the caller
-// runs the bucket path).  Leaves the filter zero.
+// Repeated rows of the column, -1 when the marks overflow (then the caller
+// runs the bucket path), or -2 when a row lies outside [0, m) (the bucket
+// passes index their counters by row and are never run on such a column).
+// Leaves the filter zero.
 template <int U>
 __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, int off, int j, bool resident, int rbeg,
-                                                     int rlen, const int32_t* my_ri, int s, uint32_t* filt,
-                                                     int32_t* stage, uint32_t* marks, int cap, int lane) {
+                                                     int rlen, const int32_t* my_ri, int s, const int* m_ptr,
+                                                     uint32_t* filt, int32_t* stage, uint32_t* marks, int cap,
+                                                     int lane) {
   FilterMark fm{filt, stage};
-  for_each_column_entry<false, U, int32_t>(in, k, off, j, resident, rbeg, rlen, my_ri, nullptr, lane, fm);
+  ChunkCache cc{{0, 0}, {0, 0}, false};
+  for_each_column_entry<false, U, int32_t>(in, k, off, j, resident, rbeg, rlen, my_ri, nullptr, lane, fm, cc);
   __syncwarp();
   constexpr int Q = 16;  // s <= 32 * Q
   // v[q] = staged row of position lane + 32q (INT32_MAX past s: no valid
   // row equals it, since rows are below m < 2^31 - 1).
   int32_t v[Q];
   uint32_t mine = 0u;  // bit q: position lane + 32q is marked
+  uint32_t top = 0u;   // largest row with the mark bit cleared (a negative row lands at 2^31 - 1 or near)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int e = lane + 32 * q;
@@ -304,8 +331,10 @@ __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, in
     if (e < s) {
       filt[filter_hash(v[q] & INT32_MAX) >> 5] = 0u;  // clear the filter for the next column
       if (v[q] < 0) mine |= 1u << q;
+      top = max(top, (uint32_t)(v[q] & INT32_MAX));
     }
   }
+  if (__any_sync(SPK_FULL, top >= (uint32_t)*m_ptr)) return -2;
   // List the marked positions: per-lane counts, one warp scan, then each
   // lane writes its own (few) positions.
   const int cnt = __popc(mine);
@@ -336,6 +365,96 @@ __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, in
   return reps;
 }
 
+// Exclusive scan of the NB bucket counts into bucket starts (in place); the
+// buckets holding two or more entries -- the only ones that need sorting --
+// are listed in mlist as (start | size << 16).  Returns their number.
+__device__ __forceinline__ int bucket_scan(uint32_t* cnt, uint32_t* mlist, int NB, int lane) {
+  int nmulti = 0;
+  const int per = NB >> 5;
+  const int b0 = lane * per;
+  int loc = 0;
+  for (int t = 0; t < per; ++t) loc += (int)cnt[pad16(b0 + t)];
+  const int inc = warp_incl_scan(loc, lane);
+  int run = inc - loc;
+  for (int t = 0; t < per; ++t) {
+    const int p = pad16(b0 + t);
+    const int x = (int)cnt[p];
+    cnt[p] = (uint32_t)run;
+    const bool multi = x >= 2;
+    const unsigned bal = __ballot_sync(SPK_FULL, multi);
+    if (multi) mlist[nmulti + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)run | ((uint32_t)x << 16);
+    nmulti += __popc(bal);
+    run += x;
+  }
+  return nmulti;
+}
+
+// Insertion sort of the listed multi-entry buckets, one bucket per lane (they
+// hold 2-3 entries mostly).  Returns this lane's count of repeated rows met
+// (the symbolic count uses it).
+template <typename V, bool NUMERIC>
+__device__ __forceinline__ int sort_buckets(int32_t* skey, V* sval, const uint32_t* mlist, int nmulti, int lane) {
+  int dups = 0;
+  for (int i = lane; i < nmulti; i += 32) {
+    const uint32_t w = mlist[i];
+    const int lo = (int)(w & 0xffffu), hi = lo + (int)(w >> 16);
+    for (int x = lo + 1; x < hi; ++x) {
+      const int32_t kx = skey[x];
+      V vx;
+      if constexpr (NUMERIC) vx = sval[x];
+      int y = x - 1;
+      while (y >= lo && skey[y] > kx) {
+        skey[y + 1] = skey[y];
+        if constexpr (NUMERIC) sval[y + 1] = sval[y];
+        --y;
+      }
+      skey[y + 1] = kx;
+      if constexpr (NUMERIC) sval[y + 1] = vx;
+    }
+    if constexpr (!NUMERIC)
+      for (int x = lo + 1; x < hi; ++x) dups += skey[x] == skey[x - 1];
+  }
+  return dups;
+}
+
+// The s slots hold the column's entries sorted by row: write B(:,j).  Without
+// repeated rows (u == s) the slots are copied out; otherwise a row's first
+// slot is its leader, which sums its run of equal rows and writes at (leaders
+// before it) = ballot prefix.
+template <typename V>
+__device__ __forceinline__ void write_sorted(const int32_t* skey, const V* sval, int s, int u, bool force_dedup,
+                                             int32_t* out_row, V* out_val, Counters* ctr_w, int lane) {
+  if (!force_dedup && u == s) {
+    for (int q = lane; q < s; q += 32) {
+      out_row[q] = skey[q];
+      out_val[q] = sval[q];
+    }
+    return;
+  }
+  int before = 0;
+  int32_t carry = -1;  // last row of the previous 32 slots
+  for (int q0 = 0; q0 < s; q0 += 32) {
+    const int q = q0 + lane;
+    const int32_t key = q < s ? skey[q] : -2;
+    int32_t prev = __shfl_up_sync(SPK_FULL, key, 1);
+    if (lane == 0) prev = carry;
+    const bool lead = q < s && key != prev;
+    const unsigned bal = __ballot_sync(SPK_FULL, lead);
+    if (lead) {
+      V sum = sval[q];
+      for (int y = q + 1; y < s && skey[y] == key; ++y) sum += sval[y];
+      const int pos = before + __popc(bal & ((1u << lane) - 1u));
+      if (pos < u) {
+        out_row[pos] = key;
+        out_val[pos] = sum;
+      }
+    }
+    before += __popc(bal);
+    carry = __shfl_sync(SPK_FULL, key, 31);
+  }
+  if (before != u && lane == 0) atomicOr(&ctr_w->err, ERR_INTERNAL);  // symbolic and numeric disagree
+}
+
 // Per-warp shared buffers.
 struct WarpSmem {
   unsigned char* vals;  // numeric values
@@ -362,103 +481,35 @@ __device__ __forceinline__ int warp_column(const Inputs& in, const WarpColArgs& 
   __syncwarp();
   // Pass 1: entries per bucket.
   BucketCount<V> count{cnt, mul};
-  for_each_column_entry<false, U, V>(in, k, off, j, resident, cur.beg, cur.len, my_ri, my_va, lane, count);
+  ChunkCache cc{{0, 0}, {0, 0}, false};
+  for_each_column_entry<false, U, V>(in, k, off, j, resident, cur.beg, cur.len, my_ri, my_va, lane, count, cc);
   __syncwarp();
-  // Scan the counts into bucket starts; list the buckets with two or more
-  // entries on the way (they are the only ones that need sorting).
-  int nmulti = 0;
-  {
-    const int per = NB >> 5;
-    const int b0 = lane * per;
-    int loc = 0;
-    for (int t = 0; t < per; ++t) loc += (int)cnt[pad16(b0 + t)];
-    const int inc = warp_incl_scan(loc, lane);
-    int run = inc - loc;
-    for (int t = 0; t < per; ++t) {
-      const int p = pad16(b0 + t);
-      const int x = (int)cnt[p];
-      cnt[p] = (uint32_t)run;
-      const bool multi = x >= 2;
-      const unsigned bal = __ballot_sync(SPK_FULL, multi);
-      if (multi) mlist[nmulti + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)run | ((uint32_t)x << 16);
-      nmulti += __popc(bal);
-      run += x;
-    }
-  }
+  int nmulti = bucket_scan(cnt, mlist, NB, lane);
   __syncwarp();
   // Pass 2: file every entry at its bucket's next slot.
   BucketFile<V, NUMERIC> file{cnt, skey, sval, mul};
-  for_each_column_entry<NUMERIC, U, V>(in, k, off, j, resident, cur.beg, cur.len, my_ri, my_va, lane, file);
+  for_each_column_entry<NUMERIC, U, V>(in, k, off, j, resident, cur.beg, cur.len, my_ri, my_va, lane, file, cc);
   __syncwarp();
   // Sort the multi-entry buckets, one bucket per lane (insertion sort; they
   // hold 2-3 entries mostly).  Symbolic: count the repeated rows met.
-  int dups = 0;
   // Unsorted output and no repeated row: the bucket order is all that is kept.
   if (NUMERIC && a.unsorted_out && cur.u == s) nmulti = 0;
-  for (int i = lane; i < nmulti; i += 32) {
-    const uint32_t w = mlist[i];
-    const int lo = (int)(w & 0xffffu), hi = lo + (int)(w >> 16);
-    for (int x = lo + 1; x < hi; ++x) {
-      const int32_t kx = skey[x];
-      V vx;
-      if constexpr (NUMERIC) vx = sval[x];
-      int y = x - 1;
-      while (y >= lo && skey[y] > kx) {
-        skey[y + 1] = skey[y];
-        if constexpr (NUMERIC) sval[y + 1] = sval[y];
-        --y;
-      }
-      skey[y + 1] = kx;
-      if constexpr (NUMERIC) sval[y + 1] = vx;
-    }
-    if constexpr (!NUMERIC)
-      for (int x = lo + 1; x < hi; ++x) dups += skey[x] == skey[x - 1];
-  }
+  const int dups = sort_buckets<V, NUMERIC>(skey, sval, mlist, nmulti, lane);
   __syncwarp();
   if constexpr (!NUMERIC) return warp_sum(dups);
-  // The s slots now hold the column's entries sorted by row.  A row's first
-  // slot is its leader; leaders before slot q = ballot prefix.
   if constexpr (NUMERIC) {
-    const int u = cur.u;
-    V* out_val = static_cast<V*>(out_val_raw);
-    if (!a.force_dedup && u == s) {
-      for (int q = lane; q < s; q += 32) {  // no repeated row: copy out
-        out_row[q] = skey[q];
-        out_val[q] = sval[q];
-      }
-    } else {
-      int before = 0;
-      int32_t carry = -1;  // last row of the previous 32 slots
-      for (int q0 = 0; q0 < s; q0 += 32) {
-        const int q = q0 + lane;
-        const int32_t key = q < s ? skey[q] : -2;
-        int32_t prev = __shfl_up_sync(SPK_FULL, key, 1);
-        if (lane == 0) prev = carry;
-        const bool lead = q < s && key != prev;
-        const unsigned bal = __ballot_sync(SPK_FULL, lead);
-        if (lead) {
-          V sum = sval[q];
-          for (int y = q + 1; y < s && skey[y] == key; ++y) sum += sval[y];
-          const int pos = before + __popc(bal & ((1u << lane) - 1u));
-          if (pos < u) {
-            out_row[pos] = key;
-            out_val[pos] = sum;
-          }
-        }
-        before += __popc(bal);
-        carry = __shfl_sync(SPK_FULL, key, 31);
-      }
-      if (before != u && lane == 0) atomicOr(&a.ctr_w->err, ERR_INTERNAL);  // symbolic and numeric disagree
-    }
+    write_sorted<V>(skey, sval, s, cur.u, a.force_dedup, out_row, static_cast<V*>(out_val_raw), a.ctr_w, lane);
     return 0;
   }
 }
 
 // DT: 0 = float values, 1 = double values (a batch mixing both runs the
 // numeric kernel once per dtype, skipping the other dtype's columns).  BATCH:
-// columns of several problems (looked up per column); otherwise one problem,
-// whose inputs' pointers lanes may hold for the whole launch (resident mode).
-template <int DT, bool NUMERIC, bool BATCH, int WARPS, int U>
+// columns of several problems (looked up per column); otherwise one problem.
+// RES (one problem with k <= 32): lanes hold the inputs' pointers for the
+// whole launch (resident mode); the host picks it, so each instantiation
+// carries only the code of its mode.
+template <int DT, bool NUMERIC, bool BATCH, bool RES, int WARPS, int U>
 __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColArgs a) {
   using VB = typename std::conditional<DT == 1, double, float>::type;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -476,11 +527,17 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColAr
     __syncwarp();
   }
   __shared__ uint32_t s_mul[16];
+  __shared__ int s_m0;
   if (!BATCH && threadIdx.x < 16) s_mul[threadIdx.x] = in.inst[0].bucket_mul[threadIdx.x];
+  if (!BATCH && threadIdx.x == 0) s_m0 = in.inst[0].m;
   __syncthreads();
   const int ncols = a.ctr->n_warp;
   const int k0 = in.inst[0].k;
-  const bool resident = !BATCH && k0 <= 32;
+  const bool resident = RES;
+  if (RES && (BATCH || k0 > 32)) {  // the host never launches this; never index lanes past k
+    if (threadIdx.x == 0) atomicOr(&a.ctr_w->err, ERR_INTERNAL);
+    return;
+  }
   const int32_t* my_cp = nullptr;
   const int32_t* my_ri = nullptr;
   const void* my_va = nullptr;
@@ -512,9 +569,14 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColAr
       if constexpr (!NUMERIC) {
         int dups = -1;
         if (cur.s <= 512)
-          dups = warp_repeats_filtered<U>(in, k, off, j, resident, cur.beg, cur.len, my_ri, cur.s, sm.filt, sm.skey,
-                                          sm.mlist, min(MARK_MAX, smax / 2 + 1), lane);
+          dups = warp_repeats_filtered<U>(in, k, off, j, resident, cur.beg, cur.len, my_ri, cur.s,
+                                          BATCH ? &I->m : &s_m0, sm.filt, sm.skey, sm.mlist,
+                                          min(MARK_MAX, smax / 2 + 1), lane);
         __syncwarp();
+        if (dups == -2) {  // a row outside [0, m): reported; B is never computed
+          if (lane == 0) atomicOr(&a.ctr_w->err, ERR_RANGE);
+          dups = 0;
+        }
         if (dups < 0)
           dups = warp_column<int32_t, false, U>(in, a, sm, cur, k, off, j, mul, NB, nullptr, nullptr, resident,
                                                 my_ri, my_va, lane);
@@ -564,8 +626,10 @@ static cudaError_t launch_warp_col(const Inputs& in, WarpColArgs a, int warp_max
   constexpr int WARPS = 8;
   a.smax = pow2_at_least(warp_max) < 32 ? 32 : pow2_at_least(warp_max);
   const size_t smem = (size_t)WARPS * warp_col_bytes<VB, NUMERIC>(a.smax);
-  auto kern = in.col_inst ? k_warp_col<DT, NUMERIC, true, WARPS, NUMERIC ? 8 : 16>
-                          : k_warp_col<DT, NUMERIC, false, WARPS, NUMERIC ? 8 : 16>;
+  constexpr int U = NUMERIC ? 8 : 16;
+  auto kern = in.col_inst ? k_warp_col<DT, NUMERIC, true, false, WARPS, U>
+              : in.kmax <= 32 ? k_warp_col<DT, NUMERIC, false, true, WARPS, U>
+                              : k_warp_col<DT, NUMERIC, false, false, WARPS, U>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int grid = dev.sms * blocks_per_sm(dev, smem + 128, WARPS * 32);

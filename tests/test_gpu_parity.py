@@ -206,6 +206,24 @@ def test_validate_rejects_row_out_of_range():
     assert e.value.status == 4
 
 
+@pytest.mark.parametrize("bad_row", [10, 4096, -5, 2**31 - 1])
+@pytest.mark.parametrize("batch", [False, True])
+def test_row_out_of_range_in_warp_column_reported_without_validation(bad_row, batch):
+    """validate = 0: a warp-class column holding a row outside [0, m) is caught
+    by the symbolic pass (its bucket passes index shared counters by row and
+    must not run on it); spkadd_symbolic reports SPKADD_ERR_INDEX_RANGE."""
+    cp = torch.tensor([0, 3, 5], dtype=torch.int32)
+    A = [(cp, torch.tensor([1, 4, 7, 2, 3], dtype=torch.int32), torch.ones(5, dtype=F64)),
+         (cp, torch.tensor([0, 4, bad_row, 5, 9], dtype=torch.int32), torch.ones(5, dtype=F64))]
+    Ad = [tuple(t.to("cuda:0") for t in a) for a in A]
+    with pytest.raises(spk.SpkaddError) as e:
+        if batch:
+            spk.spkadd_batch([(Ad, 10)])
+        else:
+            spk.spkadd(Ad, 10)
+    assert e.value.name == "SPKADD_ERR_INDEX_RANGE"
+
+
 def test_validate_rejects_bad_col_ptr():
     cp = torch.tensor([0, 3, 2], dtype=torch.int32)
     A = [(cp, torch.tensor([1, 2], dtype=torch.int32), torch.ones(2, dtype=F64))]
