@@ -281,6 +281,43 @@ spkadd_status spkadd_destroy(spkadd_handle* h);
 #define SPKADD_SCAN_NOALLOC_MAX_N (4096 * 4096)
 spkadd_status spkadd_scan_counts_noalloc(const int32_t* counts, int64_t n, int64_t* col_ptr, void* stream);
 
+/*
+ * Streaming accumulation.  Sec. IV (distributed SpGEMM) adds the stage
+ * results of sparse SUMMA; Sec. V notes that inputs arriving in batches, or
+ * too many to fit in memory together, can be arranged in batches with SpKAdd
+ * applied per batch.  A stream keeps the running sum B on the device; each
+ * spkadd_stream_add of k inputs is one (k+1)-way SpKAdd (the phases above)
+ * with B as input 0, so only the current batch of inputs need be resident.
+ * B stays the union of all inputs added so far, rows sorted in every column.
+ *
+ * spkadd_stream_create: B = the empty m x n matrix of `dtype`.  All device
+ *   work of the stream is ordered on `stream` (cudaStream_t as void*, NULL =
+ *   legacy default stream).  `opt` as for spkadd_plan (NULL = defaults); its
+ *   allocator, if any, also holds B.  Errors: INVALID_ARG (null s, negative
+ *   size, bad dtype or option), OVERFLOW (m or n >= 2^31), NOMEM, CUDA.
+ * spkadd_stream_add: B <- B + A[0] + ... + A[k-1] (1 <= k < SPKADD_MAX_K;
+ *   A as spkadd_plan takes them, shapes equal to the stream's).  Blocks once
+ *   (the symbolic phase); the numeric work runs on the stream afterwards, so
+ *   the inputs must stay valid until it is done.  nnz(B) must stay below
+ *   2^31 (B is the next add's input): otherwise OVERFLOW and B is unchanged.
+ *   Every error leaves B unchanged.
+ * spkadd_stream_query: nnz(B); optionally the number of adds and of kernel
+ *   launches so far.
+ * spkadd_stream_view: B as an spkadd_csc (int32 col_ptr; device memory owned
+ *   by the stream, valid until the next add or destroy).
+ * spkadd_stream_result: copies B into caller buffers (device): int64
+ *   col_ptr[n+1], row_idx[nnz], val[nnz]; asynchronous on the stream.
+ * spkadd_stream_destroy: releases B (stream-ordered); NULL is allowed.
+ */
+typedef struct spkadd_stream spkadd_stream;
+spkadd_status spkadd_stream_create(spkadd_stream** s, int64_t m, int64_t n, spkadd_dtype dtype, void* stream,
+                                   const spkadd_options* opt);
+spkadd_status spkadd_stream_add(spkadd_stream* s, int k, const spkadd_csc* A);
+spkadd_status spkadd_stream_query(spkadd_stream* s, int64_t* nnz_B, int64_t* adds, int64_t* kernel_launches);
+spkadd_status spkadd_stream_view(spkadd_stream* s, spkadd_csc* B);
+spkadd_status spkadd_stream_result(spkadd_stream* s, int64_t* B_col_ptr, int32_t* B_row_idx, void* B_val);
+spkadd_status spkadd_stream_destroy(spkadd_stream* s);
+
 /* Static, human-readable name of a status code. */
 const char* spkadd_status_string(spkadd_status s);
 

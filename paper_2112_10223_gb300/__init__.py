@@ -45,6 +45,7 @@ __all__ = [
     "spkadd_numeric", "spkadd_destroy", "spkadd_get_info", "spkadd_status_string", "spkadd", "Handle",
     "STATUS", "spkadd_scan_counts_noalloc", "SCAN_NOALLOC_MAX_N", "spkadd_batch_plan", "spkadd_batch_plan_raw",
     "spkadd_batch_symbolic", "spkadd_batch_numeric", "spkadd_batch_numeric_raw", "spkadd_batch", "BatchHandle",
+    "SpkaddStream",
 ]
 
 SCAN_NOALLOC_MAX_N = 4096 * 4096
@@ -122,6 +123,16 @@ def library():
         lib.spkadd_batch_numeric.restype = ctypes.c_int
         lib.spkadd_scan_counts_noalloc.argtypes = [P, ctypes.c_int64, P, P]
         lib.spkadd_scan_counts_noalloc.restype = ctypes.c_int
+        I64P = ctypes.POINTER(ctypes.c_int64)
+        lib.spkadd_stream_create.argtypes = [ctypes.POINTER(P), ctypes.c_int64, ctypes.c_int64, ctypes.c_int, P,
+                                             ctypes.POINTER(Options)]
+        lib.spkadd_stream_add.argtypes = [P, ctypes.c_int, ctypes.POINTER(CSC)]
+        lib.spkadd_stream_query.argtypes = [P, I64P, I64P, I64P]
+        lib.spkadd_stream_view.argtypes = [P, ctypes.POINTER(CSC)]
+        lib.spkadd_stream_result.argtypes = [P, P, P, P]
+        lib.spkadd_stream_destroy.argtypes = [P]
+        for f in ("create", "add", "query", "view", "result", "destroy"):
+            getattr(lib, "spkadd_stream_" + f).restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -174,16 +185,9 @@ def _stream_ptr(stream):
     return stream, ctypes.c_void_p(stream.cuda_stream)
 
 
-def spkadd_plan(A, m: int, dtype=None, stream=None, options: Options | None = None) -> Handle:
-    """spkadd_plan: check the inputs, allocate the workspace, bin the columns."""
-    lib = library()
-    k = len(A)
-    if k == 0:
-        _check(1, "spkadd_plan")
-    dtype = dtype or A[0][2].dtype
-    if dtype not in _DTYPE:
-        raise TypeError("values must be float32 or float64")
-    arr = (CSC * k)()
+def _csc_array(A, m: int, dtype):
+    """spkadd_csc descriptors of the inputs (and the tensors to keep alive)."""
+    arr = (CSC * len(A))()
     keep = []
     for i, (cp, ri, va) in enumerate(A):
         for t, dt in ((cp, torch.int32), (ri, torch.int32), (va, dtype)):
@@ -196,6 +200,19 @@ def spkadd_plan(A, m: int, dtype=None, stream=None, options: Options | None = No
         arr[i].row_idx = ri.data_ptr() if ri.numel() else None
         arr[i].val = va.data_ptr() if va.numel() else None
         keep.append((cp, ri, va))
+    return arr, keep
+
+
+def spkadd_plan(A, m: int, dtype=None, stream=None, options: Options | None = None) -> Handle:
+    """spkadd_plan: check the inputs, allocate the workspace, bin the columns."""
+    lib = library()
+    k = len(A)
+    if k == 0:
+        _check(1, "spkadd_plan")
+    dtype = dtype or A[0][2].dtype
+    if dtype not in _DTYPE:
+        raise TypeError("values must be float32 or float64")
+    arr, keep = _csc_array(A, m, dtype)
     stream, sp = _stream_ptr(stream)
     h = ctypes.c_void_p()
     _check(lib.spkadd_plan(ctypes.byref(h), k, arr, _DTYPE[dtype], sp,
@@ -406,3 +423,66 @@ def spkadd_batch(problems, stream=None, options: Options | None = None, info: bo
     finally:
         spkadd_destroy(h)
     return (outs, stats) if info else outs
+
+
+class SpkaddStream:
+    """spkadd_stream_*: a running sum B on the device, B <- B + (a batch of inputs) per add.
+
+    Each add is one (k+1)-way SpKAdd with B as input 0, so only the current
+    batch of inputs need be resident.  The inputs of an add are kept alive
+    until the next add (their numeric work may still be running).
+    """
+
+    def __init__(self, m: int, n: int, dtype=torch.float64, stream=None, options: Options | None = None):
+        if dtype not in _DTYPE:
+            raise TypeError("values must be float32 or float64")
+        self.m, self.n, self.dtype = int(m), int(n), dtype
+        self.stream, sp = _stream_ptr(stream)
+        self.ptr = ctypes.c_void_p()
+        self._keep = None
+        _check(library().spkadd_stream_create(ctypes.byref(self.ptr), self.m, self.n, _DTYPE[dtype], sp,
+                                              ctypes.byref(options) if options is not None else None),
+               "spkadd_stream_create")
+
+    def add(self, A) -> int:
+        """B <- B + sum(A); returns nnz(B)."""
+        if len(A) == 0:
+            _check(1, "spkadd_stream_add")
+        arr, keep = _csc_array(A, self.m, self.dtype)
+        _check(library().spkadd_stream_add(self.ptr, len(A), arr), "spkadd_stream_add")
+        self._keep = keep
+        return self.nnz
+
+    def query(self) -> dict:
+        nnz, adds, launches = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(library().spkadd_stream_query(self.ptr, ctypes.byref(nnz), ctypes.byref(adds), ctypes.byref(launches)),
+               "spkadd_stream_query")
+        return {"nnz": int(nnz.value), "adds": int(adds.value), "kernel_launches": int(launches.value)}
+
+    @property
+    def nnz(self) -> int:
+        return self.query()["nnz"]
+
+    def result(self):
+        """B as (col_ptr int64, row_idx int32, val) CUDA tensors (copies)."""
+        nnz = self.nnz
+        dev = torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.stream(self.stream):
+            cp = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+            ri = torch.empty(nnz, dtype=torch.int32, device=dev)
+            va = torch.empty(nnz, dtype=self.dtype, device=dev)
+        _check(library().spkadd_stream_result(self.ptr, cp.data_ptr(), ri.data_ptr() if nnz else None,
+                                              va.data_ptr() if nnz else None), "spkadd_stream_result")
+        return cp, ri, va
+
+    def close(self) -> None:
+        if getattr(self, "ptr", None):
+            ptr, self.ptr = self.ptr, None
+            _check(library().spkadd_stream_destroy(ptr), "spkadd_stream_destroy")
+        self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -93,6 +93,24 @@ spkadd_status from_device_err(int32_t err) {
 
 }  // namespace
 
+// Device memory through the caller's allocator (options.alloc / free), else
+// stream-ordered cudaMallocAsync / cudaFreeAsync on st.
+static void* ws_alloc(const spkadd_options& o, cudaStream_t st, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (o.alloc) return o.alloc(bytes, (void*)st, o.alloc_ctx);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+static void ws_free(const spkadd_options& o, cudaStream_t st, void* p) {
+  if (!p) return;
+  if (o.alloc) o.free(p, (void*)st, o.alloc_ctx);
+  else cudaFreeAsync(p, st);
+}
+
 struct spkadd_handle {
   bool batch = false;       // made by spkadd_batch_plan
   int count = 0;            // problems (1 for spkadd_plan)
@@ -131,21 +149,8 @@ struct spkadd_handle {
   int state = 0;
   int64_t launches = 0;  // kernels launched by this handle
 
-  void* dev_alloc(size_t bytes) {
-    if (bytes == 0) bytes = 256;
-    if (opt.alloc) return opt.alloc(bytes, (void*)st, opt.alloc_ctx);
-    void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    return p;
-  }
-  void dev_free(void* p) {
-    if (!p) return;
-    if (opt.alloc) opt.free(p, (void*)st, opt.alloc_ctx);
-    else cudaFreeAsync(p, st);
-  }
+  void* dev_alloc(size_t bytes) { return ws_alloc(opt, st, bytes); }
+  void dev_free(void* p) { ws_free(opt, st, p); }
 };
 
 SPK_API void spkadd_default_options(spkadd_options* opt) {
@@ -587,5 +592,161 @@ SPK_API spkadd_status spkadd_destroy(spkadd_handle* h) {
   h->dev_free(h->offs_buf);
   h->dev_free(h->ws);
   delete h;
+  return SPKADD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Streaming accumulation (Sec. IV, distributed SpGEMM: the stage results of
+// sparse SUMMA are added; Sec. V: inputs that arrive in batches, or do not fit
+// in memory together, are arranged in batches and each batch is added with
+// SpKAdd).  The stream keeps the running sum B on the device; each add of k
+// inputs is one (k+1)-way SpKAdd with B as input 0, so only one batch of
+// inputs need be resident at a time.
+// ---------------------------------------------------------------------------
+struct spkadd_stream {
+  int64_t m = 0, n = 0;
+  spkadd_dtype dtype = SPKADD_F64;
+  cudaStream_t st = nullptr;
+  spkadd_options opt{};
+  int sms = 1;
+  int32_t* cp = nullptr;  // running sum B: int32 col_ptr[n + 1], rows, values
+  int32_t* ri = nullptr;
+  void* va = nullptr;
+  int64_t nnz = 0;
+  int64_t adds = 0;
+  int64_t launches = 0;   // kernels launched by the stream's adds and reads
+};
+
+SPK_API spkadd_status spkadd_stream_create(spkadd_stream** sp, int64_t m, int64_t n, spkadd_dtype dtype, void* stream,
+                                           const spkadd_options* opt) {
+  if (!sp) return SPKADD_ERR_INVALID_ARG;
+  *sp = nullptr;
+  if (m < 0 || n < 0) return SPKADD_ERR_INVALID_ARG;
+  if (m >= INT32_MAX || n >= INT32_MAX) return SPKADD_ERR_OVERFLOW;
+  if (dtype != SPKADD_F32 && dtype != SPKADD_F64) return SPKADD_ERR_INVALID_ARG;
+  spkadd_options o;
+  spkadd_default_options(&o);
+  if (opt) o = *opt;
+  const spkadd_status cs = check_options(o);
+  if (cs != SPKADD_OK) return cs;
+  int device = 0, sms = 0;
+  cudaError_t ce = cudaGetDevice(&device);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (ce != cudaSuccess) return from_cuda(ce);
+  spkadd_stream* s = new (std::nothrow) spkadd_stream;
+  if (!s) return SPKADD_ERR_NOMEM;
+  s->m = m;
+  s->n = n;
+  s->dtype = dtype;
+  s->st = static_cast<cudaStream_t>(stream);
+  s->opt = o;
+  s->sms = sms > 0 ? sms : 1;
+  s->cp = static_cast<int32_t*>(ws_alloc(o, s->st, (size_t)(n + 1) * sizeof(int32_t)));
+  if (!s->cp) {
+    delete s;
+    return SPKADD_ERR_NOMEM;
+  }
+  ce = cudaMemsetAsync(s->cp, 0, (size_t)(n + 1) * sizeof(int32_t), s->st);  // B = 0: every column empty
+  if (ce != cudaSuccess) {
+    ws_free(o, s->st, s->cp);
+    delete s;
+    return from_cuda(ce);
+  }
+  *sp = s;
+  return SPKADD_OK;
+}
+
+SPK_API spkadd_status spkadd_stream_add(spkadd_stream* s, int k, const spkadd_csc* A) {
+  if (!s || k < 1 || !A) return SPKADD_ERR_INVALID_ARG;
+  if (k >= SPKADD_MAX_K) return SPKADD_ERR_UNSUPPORTED;  // k + 1 inputs with the running sum
+  for (int i = 0; i < k; ++i)
+    if (A[i].m != s->m || A[i].n != s->n) return SPKADD_ERR_SHAPE_MISMATCH;
+  std::vector<spkadd_csc> all;
+  try {
+    all.resize((size_t)k + 1);
+  } catch (...) {
+    return SPKADD_ERR_NOMEM;
+  }
+  all[0] = spkadd_csc{s->m, s->n, s->nnz, s->cp, s->nnz ? s->ri : nullptr, s->nnz ? s->va : nullptr};
+  for (int i = 0; i < k; ++i) all[(size_t)i + 1] = A[i];
+  spkadd_handle* h = nullptr;
+  spkadd_status r = spkadd_plan(&h, k + 1, all.data(), s->dtype, (void*)s->st, &s->opt);
+  if (r != SPKADD_OK) return r;
+  int64_t nnz = 0;
+  r = spkadd_symbolic(h, &nnz);
+  if (r == SPKADD_OK && nnz > INT32_MAX) r = SPKADD_ERR_OVERFLOW;  // the sum must stay usable as an input
+  int32_t* cp = nullptr;
+  int32_t* ri = nullptr;
+  void* va = nullptr;
+  if (r == SPKADD_OK) {
+    const size_t vs = s->dtype == SPKADD_F64 ? 8 : 4;
+    cp = static_cast<int32_t*>(ws_alloc(s->opt, s->st, (size_t)(s->n + 1) * sizeof(int32_t)));
+    ri = static_cast<int32_t*>(ws_alloc(s->opt, s->st, (size_t)nnz * sizeof(int32_t)));
+    va = ws_alloc(s->opt, s->st, (size_t)nnz * vs);
+    if (!cp || !ri || !va) r = SPKADD_ERR_NOMEM;
+  }
+  if (r == SPKADD_OK) {
+    const cudaError_t ce = spk::launch_colptr_narrow(h->d_colptr, cp, s->n + 1, s->sms, s->st);
+    if (ce != cudaSuccess) r = from_cuda(ce);
+  }
+  if (r == SPKADD_OK) {
+    spk::Outs out{};
+    out.row0 = ri;
+    out.val0 = va;
+    r = run_numeric(h, out);
+  }
+  if (r == SPKADD_OK) s->launches += h->launches + 1;
+  spkadd_destroy(h);  // stream-ordered: its workspace is released after the kernels above
+  if (r != SPKADD_OK) {
+    ws_free(s->opt, s->st, cp);
+    ws_free(s->opt, s->st, ri);
+    ws_free(s->opt, s->st, va);
+    return r;
+  }
+  ws_free(s->opt, s->st, s->cp);
+  ws_free(s->opt, s->st, s->ri);
+  ws_free(s->opt, s->st, s->va);
+  s->cp = cp;
+  s->ri = ri;
+  s->va = va;
+  s->nnz = nnz;
+  s->adds += 1;
+  return SPKADD_OK;
+}
+
+SPK_API spkadd_status spkadd_stream_query(spkadd_stream* s, int64_t* nnz_B, int64_t* adds, int64_t* kernel_launches) {
+  if (!s || !nnz_B) return SPKADD_ERR_INVALID_ARG;
+  *nnz_B = s->nnz;
+  if (adds) *adds = s->adds;
+  if (kernel_launches) *kernel_launches = s->launches;
+  return SPKADD_OK;
+}
+
+SPK_API spkadd_status spkadd_stream_view(spkadd_stream* s, spkadd_csc* B) {
+  if (!s || !B) return SPKADD_ERR_INVALID_ARG;
+  *B = spkadd_csc{s->m, s->n, s->nnz, s->cp, s->nnz ? s->ri : nullptr, s->nnz ? s->va : nullptr};
+  return SPKADD_OK;
+}
+
+SPK_API spkadd_status spkadd_stream_result(spkadd_stream* s, int64_t* B_col_ptr, int32_t* B_row_idx, void* B_val) {
+  if (!s || !B_col_ptr) return SPKADD_ERR_INVALID_ARG;
+  if (s->nnz > 0 && (!B_row_idx || !B_val)) return SPKADD_ERR_INVALID_ARG;
+  cudaError_t ce = spk::launch_colptr_widen(s->cp, B_col_ptr, s->n + 1, s->sms, s->st);
+  if (ce == cudaSuccess && s->nnz > 0)
+    ce = cudaMemcpyAsync(B_row_idx, s->ri, (size_t)s->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s->st);
+  if (ce == cudaSuccess && s->nnz > 0)
+    ce = cudaMemcpyAsync(B_val, s->va, (size_t)s->nnz * (s->dtype == SPKADD_F64 ? 8 : 4), cudaMemcpyDeviceToDevice,
+                         s->st);
+  if (ce != cudaSuccess) return from_cuda(ce);
+  s->launches += 1;
+  return SPKADD_OK;
+}
+
+SPK_API spkadd_status spkadd_stream_destroy(spkadd_stream* s) {
+  if (!s) return SPKADD_OK;
+  ws_free(s->opt, s->st, s->cp);
+  ws_free(s->opt, s->st, s->ri);
+  ws_free(s->opt, s->st, s->va);
+  delete s;
   return SPKADD_OK;
 }

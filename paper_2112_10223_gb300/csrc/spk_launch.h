@@ -59,6 +59,9 @@ cudaError_t launch_num_cta(const Inputs& in, int dt, const Window* win, int n_wi
 // Per-problem column pointers of B (a batch): out_cp[q][j] = col_ptr[colbase + j] - col_ptr[colbase].
 cudaError_t launch_out_colptr(const Inputs& in, const Outs& o, const int64_t* col_ptr, int sms, cudaStream_t st);
 // Per-problem nnz(B): nnz[q] = col_ptr[colbase + n] - col_ptr[colbase].
+// B's int64 column pointers to int32 (a streamed running sum; nnz < 2^31) and back.
+cudaError_t launch_colptr_narrow(const int64_t* src, int32_t* dst, int64_t n1, int sms, cudaStream_t st);
+cudaError_t launch_colptr_widen(const int32_t* src, int64_t* dst, int64_t n1, int sms, cudaStream_t st);
 cudaError_t launch_inst_nnz(const Inputs& in, const int64_t* col_ptr, int64_t* nnz, cudaStream_t st);
 
 }  // namespace spk

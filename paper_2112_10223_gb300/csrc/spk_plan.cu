@@ -305,4 +305,31 @@ cudaError_t launch_out_colptr(const Inputs& in, const Outs& o, const int64_t* co
   return cudaGetLastError();
 }
 
+// Column pointers between the int64 form of B and the int32 form of an input
+// (a streamed running sum is the next add's input 0; its nnz fits int32).
+__global__ void k_colptr_narrow(const int64_t* __restrict__ src, int32_t* __restrict__ dst, int64_t n1) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (int32_t)src[i];
+}
+__global__ void k_colptr_widen(const int32_t* __restrict__ src, int64_t* __restrict__ dst, int64_t n1) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (int64_t)src[i];
+}
+
+static int colptr_blocks(int64_t n1, int sms) {
+  int64_t b = (n1 + 255) / 256;
+  if (b > (int64_t)sms * 8) b = (int64_t)sms * 8;
+  return b < 1 ? 1 : (int)b;
+}
+
+cudaError_t launch_colptr_narrow(const int64_t* src, int32_t* dst, int64_t n1, int sms, cudaStream_t st) {
+  k_colptr_narrow<<<colptr_blocks(n1, sms), 256, 0, st>>>(src, dst, n1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colptr_widen(const int32_t* src, int64_t* dst, int64_t n1, int sms, cudaStream_t st) {
+  k_colptr_widen<<<colptr_blocks(n1, sms), 256, 0, st>>>(src, dst, n1);
+  return cudaGetLastError();
+}
+
 }  // namespace spk

@@ -197,3 +197,31 @@ def test_batch_descriptor_layout_matches_the_header():
     assert spk._CSC_NP.itemsize == ctypes.sizeof(spk.CSC) == 48
     assert [spk._CSC_NP.fields[f][1] for f in ("m", "n", "nnz", "col_ptr", "row_idx", "val")] == \
         [getattr(spk.CSC, f).offset for f in ("m", "n", "nnz", "col_ptr", "row_idx", "val")]
+
+
+@pytest.mark.parametrize("m,n,dtype,expect", [
+    (-1, 4, 1, "SPKADD_ERR_INVALID_ARG"), (4, -1, 1, "SPKADD_ERR_INVALID_ARG"), (4, 4, 2, "SPKADD_ERR_INVALID_ARG"),
+    (2**31, 4, 1, "SPKADD_ERR_OVERFLOW"), (4, 2**31 - 1, 0, "SPKADD_ERR_OVERFLOW"),
+])
+def test_stream_create_rejects_bad_arguments_without_cuda(lib, m, n, dtype, expect):
+    s = ctypes.c_void_p(1)
+    st = lib.spkadd_stream_create(ctypes.byref(s), m, n, dtype, None, None)
+    assert spk.STATUS[st] == expect
+    assert not s.value  # *s cleared on failure
+
+
+def test_stream_create_rejects_bad_options_and_null_out(lib):
+    o = spk.default_options(window_max=5000)
+    s = ctypes.c_void_p()
+    assert spk.STATUS[lib.spkadd_stream_create(ctypes.byref(s), 4, 4, 1, None, ctypes.byref(o))] == \
+        "SPKADD_ERR_INVALID_ARG"
+    assert spk.STATUS[lib.spkadd_stream_create(None, 4, 4, 1, None, None)] == "SPKADD_ERR_INVALID_ARG"
+
+
+def test_stream_calls_on_null_stream_handle(lib):
+    n = ctypes.c_int64()
+    assert spk.STATUS[lib.spkadd_stream_add(None, 1, (spk.CSC * 1)())] == "SPKADD_ERR_INVALID_ARG"
+    assert spk.STATUS[lib.spkadd_stream_query(None, ctypes.byref(n), None, None)] == "SPKADD_ERR_INVALID_ARG"
+    assert spk.STATUS[lib.spkadd_stream_view(None, None)] == "SPKADD_ERR_INVALID_ARG"
+    assert spk.STATUS[lib.spkadd_stream_result(None, None, None, None)] == "SPKADD_ERR_INVALID_ARG"
+    assert lib.spkadd_stream_destroy(None) == 0
