@@ -231,30 +231,66 @@ def barrier(world):
         dist.barrier()
 
 
+def reference_sample(args):
+    """The oracle's bounded sample of the workload: a list of problems (inputs
+    on the host), a description, and the value dtype."""
+    import synth
+
+    dev = "cuda:0" if torch.cuda.is_available() else "cpu"
+    if args.workload in WORKLOADS:
+        w = WORKLOADS[args.workload]
+        A, _ = make_inputs(w, dev, seed=args.seed)
+        S, stride = oracle_sample(A, args.oracle_cols)
+        nnz = sum(a[1].numel() for a in S)
+        return [S], f"every {stride}-th column of the workload: {len(S[0][0]) - 1} columns, {nnz} input nnz per step", \
+            "f64" if w["dtype"] == torch.float64 else "f32"
+    if args.workload == STREAM_WORKLOAD:  # the summed result of all 64 inputs, on a column sample
+        A = synth.spgemm_like(64, 1 << 18, 1 << 18, 32, seed=args.seed, dtype=torch.float32, device=dev)
+        S, stride = oracle_sample(A, min(args.oracle_cols, 1 << 14))
+        nnz = sum(a[1].numel() for a in S)
+        return [S], f"every {stride}-th column of the 64 inputs: {nnz} input nnz per step", "f32"
+    # batched / served workloads: the instances in seed order, up to about 3e7 input nnz
+    if args.workload == BATCH_WORKLOAD:
+        params = synth.batch_instance_params(args.batch_count, seed=args.seed)
+    else:
+        params = synth.batch_instance_params(args.serve_requests, seed=args.seed, k_range=(2, 512),
+                                             mn_range=(1 << 10, 1 << 18))
+    probs, nnz = [], 0
+    for p in params:  # in seed order, every instance that still fits the budget
+        if nnz + synth.instance_nnz_estimate(p) > 3e7:
+            continue
+        A, _ = synth.instance(p, "cpu")
+        probs.append(A)
+        nnz += sum(a[1].numel() for a in A)
+    return probs, (f"{len(probs)} instances of the workload, in seed order those that fit a 3e7-nnz budget "
+                   f"({nnz} input nnz per step)"), "f32+f64"
+
+
 def run_reference(args, world, rank):
     """Reference arm: the CPU oracle on a bounded sample, rank 0 only."""
     if rank != 0:
         return
-    w = WORKLOADS[args.workload]
-    dev = "cuda:0" if torch.cuda.is_available() else "cpu"
-    A, _ = make_inputs(w, dev, seed=args.seed)
-    S, stride = oracle_sample(A, args.oracle_cols)
-    del A
-    nnz = sum(a[1].numel() for a in S)
-    for _ in range(args.warmup):
-        time_oracle(S, repeat=1)
-    ts = []
+    probs, sample, dtype = reference_sample(args)
+    nnz = sum(a[1].numel() for A in probs for a in A)
     cores = 1
-    for _ in range(args.steps):
-        _, t, cores, _ = time_oracle(S, repeat=1)
-        ts.append(t)
+
+    def once():
+        nonlocal cores
+        t = 0.0
+        for A in probs:
+            _, ti, cores, _ = time_oracle(A, repeat=1)
+            t += ti
+        return t
+
+    for _ in range(args.warmup):
+        once()
+    ts = [once() for _ in range(args.steps)]
     t = sum(ts) / len(ts)
     val = nnz / t
-    sample = f"every {stride}-th column of the workload: {len(S[0][0]) - 1} columns, {nnz} input nnz per step"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "nnz/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w["dtype"] == torch.float64 else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic", "config": {"workload": args.workload},
         "cpu_baseline": {"value": val, "unit": "nnz/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
