@@ -116,3 +116,44 @@ def test_stream_errors_leave_the_sum_unchanged():
     got = tuple(t.cpu().numpy() for t in s.result())
     s.close()
     compare(got, oracle.add(to_np(A)), F64, exact=True)
+
+
+def test_stream_user_allocator_holds_the_sum_and_releases_everything():
+    """With options.alloc / free, the running sum and every add's workspace come
+    from the caller's allocator; after close every allocation is returned, and
+    a failing allocator leaves the sum unchanged."""
+    A = synth.random_csc(6, 200, 40, density=0.1, seed=18, dtype=F64, value_kind="int8")
+    live, count, failing = {}, [0], [False]
+
+    @spk.ALLOC_FN
+    def alloc(nbytes, stream, ctx):
+        if failing[0]:
+            return None
+        t = torch.empty(nbytes, dtype=torch.uint8, device=DEV)
+        live[t.data_ptr()] = t
+        count[0] += 1
+        return t.data_ptr()
+
+    @spk.FREE_FN
+    def free(ptr, stream, ctx):
+        live.pop(ptr, None)
+
+    o = spk.default_options()
+    o.alloc, o.free = alloc, free
+    s = spk.SpkaddStream(200, 40, dtype=F64, options=o)
+    s.add(_dev(A[:3]))
+    before = tuple(t.cpu().numpy() for t in s.result())
+    failing[0] = True
+    with pytest.raises(spk.SpkaddError) as e:
+        s.add(_dev(A[3:]))
+    assert e.value.name == "SPKADD_ERR_NOMEM"
+    failing[0] = False
+    assert all(np.array_equal(x, y) for x, y in zip(before, (t.cpu().numpy() for t in s.result())))
+    s.add(_dev(A[3:]))
+    got = tuple(t.cpu().numpy() for t in s.result())
+    torch.cuda.synchronize()
+    assert len(live) == 3 and count[0] > 3  # the sum's col_ptr, rows and values remain
+    s.close()
+    torch.cuda.synchronize()
+    assert len(live) == 0
+    compare(got, oracle.add(to_np(A)), F64, exact=True)
