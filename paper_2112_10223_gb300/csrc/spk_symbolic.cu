@@ -113,7 +113,7 @@ constexpr int FILTER_SEG = 64;
 // non-empty words gives nnz(B(:,j)) and cuts the column into windows of at
 // most win_target + 63 distinct rows (boundaries on 64-row words).
 template <int BLOCK, int U>
-__global__ void __launch_bounds__(BLOCK) k_sym_heavy(Inputs in, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(BLOCK, BLOCK >= 1024 ? 1 : 4) k_sym_heavy(Inputs in, const int32_t* __restrict__ list,
                                                      const int32_t* __restrict__ s_arr,
                                                      const Counters* __restrict__ ctr, int32_t* __restrict__ u_out,
                                                      Window* __restrict__ win, int32_t* __restrict__ search_list,
@@ -540,7 +540,7 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const int32_
   // Small slabs: 256-thread blocks, several columns in flight per SM; a slab
   // bitmap that fills the SM: one 1024-thread block.
   const bool small = smem * 2 + 4096 <= (size_t)dev.smem_per_sm / 2;
-  auto kern = small ? k_sym_heavy<256, 8> : k_sym_heavy<HEAVY_BLOCK, 4>;
+  auto kern = small ? k_sym_heavy<256, 8> : k_sym_heavy<HEAVY_BLOCK, 8>;
   auto kern_c = k_sym_heavy_compact<256, 8>;
   const int block = small ? 256 : HEAVY_BLOCK;
   int bf = 0, bc = 0;
