@@ -23,6 +23,11 @@
 // The bitmap covers a slab of 2^slab_log2 rows (at most 2^20): an item whose
 // rows span more is processed slab by slab, with per-input binary searches
 // for each slab's entries.
+//
+// A second layout, the compact word table (k_num_compact, below), keeps only
+// a summary bit per 32-row word and a table of the item's non-empty words, so
+// its shared memory follows window_max instead of the slab; the launcher runs
+// whichever layout has more blocks resident per SM.
 #include <mutex>
 #include <type_traits>
 

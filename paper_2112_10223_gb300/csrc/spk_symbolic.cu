@@ -8,7 +8,9 @@
 //   which Sec. II-D allows in place of the hash).  Popcounts give nnz(B(:,j))
 //   and cut the column into row windows of fewer than window_max distinct rows
 //   each (Alg. 7/8's sliding windows, sized to shared memory and balanced by
-//   count rather than by equal row ranges).
+//   count rather than by equal row ranges).  An optional compact form
+//   (k_sym_heavy_compact) does the same from a summary bit per 32-row word
+//   and a bounded table of non-empty words.
 #include "spk_common.cuh"
 #include "spk_launch.h"
 
