@@ -308,6 +308,8 @@ spkadd_status spkadd_scan_counts_noalloc(const int32_t* counts, int64_t n, int64
  * spkadd_stream_result: copies B into caller buffers (device): int64
  *   col_ptr[n+1], row_idx[nnz], val[nnz]; asynchronous on the stream.
  * spkadd_stream_destroy: releases B (stream-ordered); NULL is allowed.
+ * Like a handle, a stream is not thread-safe; distinct streams are
+ * independent.
  */
 typedef struct spkadd_stream spkadd_stream;
 spkadd_status spkadd_stream_create(spkadd_stream** s, int64_t m, int64_t n, spkadd_dtype dtype, void* stream,
