@@ -584,6 +584,7 @@ def run_batch(args, world, rank, local):
     lat_req = []
     tuned = None
     tune_log = []
+    wave_log = []
     verified = 0
     oracle_nnz, oracle_t, oracle_cores = 0, 0.0, 0
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -638,6 +639,7 @@ def run_batch(args, world, rank, local):
         # one call per instance, in seed order, each waited for
         spk.spkadd(probs[0][0], probs[0][1])
         torch.cuda.synchronize()
+        t_req_wave = 0.0
         for i, (A, m) in enumerate(probs):
             t0 = time.perf_counter()
             spk.spkadd(A, m, options=opt)
@@ -645,10 +647,14 @@ def run_batch(args, world, rank, local):
             t = time.perf_counter() - t0
             lat_req.append(t)
             tot["t_req"] += t
+            t_req_wave += t
             q = wave[i]
             dec[decile[q]]["t_req"] += t
             dec[decile[q]]["instances"] += 1
             dec[decile[q]]["nnz"] += int(nnz_in[i])
+        wave_log.append({"wave": wi, "instances": len(wave), "first_instance": wave[0], "nnz_in": int(nnz_in.sum()),
+                         "batch_ms": t_batch * 1e3, "per_request_ms": t_req_wave * 1e3,
+                         "nnz_per_s": float(nnz_in.sum()) / t_batch, "speedup": t_req_wave / t_batch})
         # verification of a few instances against the oracle (not timed)
         if rank == 0 and args.batch_verify > 0:
             import oracle
@@ -720,6 +726,10 @@ def run_batch(args, world, rank, local):
                          "speedup": (x["t_req"] / x["t_batch"]) if x["t_batch"] > 0 else None}
                         for d, x in enumerate(dec)],
             "verified_instances": verified,
+            "waves": wave_log,
+            # Wave 0 is the longest seed-order prefix of the instances whose
+            # inputs fit one wave's budget, run as one batch (one set of launches).
+            "prefix_single_launch": wave_log[0] if wave_log else None,
         },
         "cpu_baseline": ({"value": oracle_nnz / oracle_t, "unit": "nnz/s", "cores": oracle_cores, "kind": "oracle",
                           "sample": f"{verified} verified instances, {oracle_nnz} input nnz, {oracle_t:.2f} s"}
