@@ -55,7 +55,7 @@ typedef enum spkadd_status {
     SPKADD_ERR_CUDA = 7,            /* a CUDA runtime call or kernel launch failed */
     SPKADD_ERR_TIMEOUT = 8,         /* a bounded device wait gave up */
     SPKADD_ERR_STATE = 9,           /* call out of order */
-    SPKADD_ERR_UNSUPPORTED = 10,    /* valid request this build does not handle (e.g. k > SPKADD_MAX_K) */
+    SPKADD_ERR_UNSUPPORTED = 10,    /* valid request this library does not handle (e.g. k > SPKADD_MAX_K) */
     SPKADD_ERR_INTERNAL = 11        /* a device-side size invariant failed; the result is not valid */
 } spkadd_status;
 

@@ -177,7 +177,7 @@ SPK_API const char* spkadd_status_string(spkadd_status s) {
     case SPKADD_ERR_CUDA: return "SPKADD_ERR_CUDA: CUDA call or kernel launch failed";
     case SPKADD_ERR_TIMEOUT: return "SPKADD_ERR_TIMEOUT: bounded device wait gave up";
     case SPKADD_ERR_STATE: return "SPKADD_ERR_STATE: call out of order";
-    case SPKADD_ERR_UNSUPPORTED: return "SPKADD_ERR_UNSUPPORTED: request not supported by this build";
+    case SPKADD_ERR_UNSUPPORTED: return "SPKADD_ERR_UNSUPPORTED: request not supported by this library";
     case SPKADD_ERR_INTERNAL: return "SPKADD_ERR_INTERNAL: device-side invariant failed";
   }
   return "SPKADD_ERR_?: unknown status";
