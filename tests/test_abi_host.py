@@ -225,3 +225,10 @@ def test_stream_calls_on_null_stream_handle(lib):
     assert spk.STATUS[lib.spkadd_stream_view(None, None)] == "SPKADD_ERR_INVALID_ARG"
     assert spk.STATUS[lib.spkadd_stream_result(None, None, None, None)] == "SPKADD_ERR_INVALID_ARG"
     assert lib.spkadd_stream_destroy(None) == 0
+
+
+def test_stream_class_rejects_bad_dtype_before_cuda(lib):
+    import torch
+
+    with pytest.raises(TypeError):
+        spk.SpkaddStream(4, 4, dtype=torch.int32)

@@ -267,6 +267,29 @@ def test_union_sizes_and_listed_columns():
         assert np.array_equal(part["val"][c:d], full["val"][a:b])
 
 
+@pytest.mark.parametrize("groups", [[2, 3, 1], [1, 1, 1, 1, 1, 1], [6]])
+def test_sum_taken_batch_by_batch_equals_one_shot(groups):
+    """Streaming reading (Sec. V: inputs added batch by batch): feeding each
+    partial sum back as an input gives the one-shot sum -- the same pattern
+    (a union of unions is the union) and, for small integers, the same values
+    exactly (integer sums are exact in any grouping)."""
+    A = _np_inputs(synth.random_csc(6, 40, 25, density=0.25, seed=9, value_kind="int8"))
+    want = oracle.add(A)
+    run = None
+    i = 0
+    for g in groups:
+        batch = A[i:i + g]
+        i += g
+        if run is not None:
+            batch = [(run["col_ptr"].astype(np.int32), run["row_idx"], run["val"])] + batch
+        run = oracle.add(batch)
+    assert np.array_equal(run["col_ptr"], want["col_ptr"])
+    assert np.array_equal(run["row_idx"], want["row_idx"])
+    assert np.array_equal(run["val"], want["val"])
+    cp, r, v, _ = brute_force(A, 40, 25)
+    assert np.array_equal(run["row_idx"], r) and np.array_equal(run["val"], v)
+
+
 def test_output_columns_sorted_strictly():
     A = _np_inputs(synth.rmat(6, 8, 8, seed=1))
     B = oracle.add(A)
