@@ -321,17 +321,20 @@ __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, in
   constexpr int Q = 16;  // s <= 32 * Q
   // v[q] = staged row of position lane + 32q (INT32_MAX past s: no valid
   // row equals it, since rows are below m < 2^31 - 1).
+  // v[q] keeps the row without its mark bit; the marks live in `mine`, so the
+  // comparisons below need no masking.
   int32_t v[Q];
   uint32_t mine = 0u;  // bit q: position lane + 32q is marked
-  uint32_t top = 0u;   // largest row with the mark bit cleared (a negative row lands at 2^31 - 1 or near)
+  uint32_t top = 0u;   // largest row (a negative row, mark bit cleared, lands at 2^31 - 1 or near)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int e = lane + 32 * q;
-    v[q] = e < s ? stage[e] : INT32_MAX;
+    const int32_t x = e < s ? stage[e] : INT32_MAX;
+    v[q] = x & INT32_MAX;
     if (e < s) {
-      filt[filter_hash(v[q] & INT32_MAX) >> 5] = 0u;  // clear the filter for the next column
-      if (v[q] < 0) mine |= 1u << q;
-      top = max(top, (uint32_t)(v[q] & INT32_MAX));
+      filt[filter_hash(v[q]) >> 5] = 0u;  // clear the filter for the next column
+      if (x < 0) mine |= 1u << q;
+      top = max(top, (uint32_t)v[q]);
     }
   }
   if (__any_sync(SPK_FULL, top >= (uint32_t)*m_ptr)) return -2;
@@ -351,13 +354,13 @@ __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, in
     // Cheap screen first: does any of this lane's rows equal xm?
     bool hit = false;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) hit |= (v[q] & INT32_MAX) == xm;
+    for (int q = 0; q < Q; ++q) hit |= v[q] == xm;
     bool found = false;
     if (hit) {  // rare: the marked entry itself, and true repeats
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const int e = lane + 32 * q;
-        if ((v[q] & INT32_MAX) == xm && e != em && (v[q] >= 0 || e < em)) found = true;
+        if (v[q] == xm && e != em && (!((mine >> q) & 1u) || e < em)) found = true;
       }
     }
     reps += __any_sync(SPK_FULL, found) ? 1 : 0;
