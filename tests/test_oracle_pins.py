@@ -290,6 +290,33 @@ def test_sum_taken_batch_by_batch_equals_one_shot(groups):
     assert np.array_equal(run["row_idx"], r) and np.array_equal(run["val"], v)
 
 
+def test_unordered_columns_and_repeats_inside_one_input():
+    """Table I: the hash method needs no sorted input.  Permuting the entries
+    inside every input column leaves the sum unchanged, and a row repeated
+    inside one input column is summed like any other term (dense brute force,
+    which adds every entry)."""
+    rng = np.random.default_rng(21)
+    A = _np_inputs(synth.random_csc(4, 30, 12, density=0.3, seed=21, value_kind="int8"))
+    want = oracle.add(A)
+    shuffled = []
+    for cp, ri, va in A:
+        ri2, va2 = ri.copy(), va.copy()
+        for j in range(len(cp) - 1):
+            perm = rng.permutation(cp[j + 1] - cp[j]) + cp[j]
+            ri2[cp[j]:cp[j + 1]], va2[cp[j]:cp[j + 1]] = ri[perm], va[perm]
+        shuffled.append((cp, ri2, va2))
+    got = oracle.add(shuffled)
+    for key in ("col_ptr", "row_idx", "val"):
+        assert np.array_equal(got[key], want[key])
+    # one input column holding row 5 three times and row 2 once, next to another input
+    rep = [(np.array([0, 4], np.int32), np.array([5, 2, 5, 5], np.int32), np.array([1.0, 2.0, 4.0, 8.0])),
+           (np.array([0, 2], np.int32), np.array([5, 7], np.int32), np.array([16.0, 32.0]))]
+    B = oracle.add(rep)
+    cp, r, v, _ = brute_force(rep, 10, 1)
+    assert np.array_equal(B["row_idx"], r) and B["row_idx"].tolist() == [2, 5, 7]
+    assert np.array_equal(B["val"], v) and B["val"].tolist() == [2.0, 29.0, 32.0]
+
+
 def test_output_columns_sorted_strictly():
     A = _np_inputs(synth.rmat(6, 8, 8, seed=1))
     B = oracle.add(A)
