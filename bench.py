@@ -460,7 +460,10 @@ def run_ours(args, world, rank, local):
                    "output_order": "any order inside a column" if args.unsorted_output else "sorted",
                    "block_accumulator": ("automatic", "flat bitmap", "compact word table")[args.block_accumulator]},
         "hbm_gbs_step": step_gbs,
-        "roofline": {"kernel": "k_warp_col<numeric> (spkadd_numeric)", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": ("k_warp_col<numeric> (spkadd_numeric)" if info["cols_cta"] + info["cols_heavy"] == 0
+                                else "spkadd_numeric: k_warp_col<numeric> and the thread-block items' kernel "
+                                     "(k_num_compact or k_num_bitmap)"),
+                     "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": read_traffic(args.workload), "algorithmic_bytes": alg,
                      "launch_ms": num_avg, "step_frac": step_gbs / peak},
