@@ -26,8 +26,8 @@
  *     device; "host" pointers to ordinary host memory.
  *   - All device work of a handle is ordered on the stream given to
  *     spkadd_plan (a cudaStream_t passed as void*; NULL = legacy default
- *     stream).  spkadd_symbolic synchronises that stream once to read nnz(B);
- *     no other call blocks the host.
+ *     stream).  spkadd_symbolic synchronises that stream once to read nnz(B),
+ *     spkadd_onepass twice; no other computing call blocks the host.
  *   - Every call returns a status; nothing aborts, throws or traps.  A failed
  *     kernel launch returns SPKADD_ERR_CUDA; errors raised asynchronously by
  *     the device surface at the next call on the handle.
@@ -145,6 +145,16 @@ typedef struct spkadd_options {
     void* (*alloc)(size_t bytes, void* stream, void* ctx);
     void (*free)(void* ptr, void* stream, void* ctx);
     void* alloc_ctx;
+    /* Longest time, in milliseconds, that any device-side wait of the
+     * one-pass kernel (spkadd_onepass: a predecessor tile's published sum)
+     * may last before the kernel gives up
+     * and the call returns SPKADD_ERR_TIMEOUT (range 1..600000). */
+    int32_t wait_timeout_ms;
+    /* Test switch, 0 in normal use.  1: in the one-pass kernel the second
+     * column tile's look-back also waits for a word that nothing writes, so
+     * its bounded wait runs out (the call returns SPKADD_ERR_TIMEOUT; nothing
+     * hangs and the device stays usable). */
+    int32_t test_stall;
 } spkadd_options;
 
 /* Planning statistics (host copy), for tests and benchmarks.  For a batch
@@ -163,13 +173,14 @@ typedef struct spkadd_info {
     int64_t workspace_bytes;
     int64_t kernel_launches; /* kernels this handle has launched so far */
     int64_t problems;       /* problems of the handle (1 unless made by spkadd_batch_plan) */
+    int64_t onepass;        /* 1 when B was last computed by the one-pass kernel (spkadd_onepass) */
 } spkadd_info;
 
 typedef struct spkadd_handle spkadd_handle;
 
 /* Fills *opt with the defaults (validate 0, warp_max 512, cta_max 4096,
- * window_max 4096, sort_mode 0, input_order 0, cudaMallocAsync).  No CUDA
- * call. */
+ * window_max 4096, sort_mode 0, input_order 0, cudaMallocAsync,
+ * wait_timeout_ms 2000, test_stall 0).  No CUDA call. */
 void spkadd_default_options(spkadd_options* opt);
 
 /*
@@ -205,6 +216,33 @@ spkadd_status spkadd_symbolic(spkadd_handle* h, int64_t* nnz_B);
  * again (with the same or other output buffers) to recompute B.
  */
 spkadd_status spkadd_numeric(spkadd_handle* h, int64_t* B_col_ptr, int32_t* B_row_idx, void* B_val);
+
+/*
+ * One-pass SpKAdd: the symbolic count (Alg. 6), the scan of Sec. II-D and the
+ * numeric sum with the per-column sort (Alg. 5) in a single pass over the
+ * inputs.  Sec. II-D needs the symbolic phase so that B can be allocated
+ * first; here B goes into buffers sized by the bound nnz(B) <= sum_i
+ * nnz(A_i) of Sec. II-A, and each column's offset in B comes from a
+ * decoupled look-back over column tiles, so every input entry is read once.
+ *   h           a handle of spkadd_plan (a batch handle: SPKADD_ERR_INVALID_ARG)
+ *   B_col_ptr   device, n+1 int64 (written)
+ *   B_row_idx   device, `capacity` int32; the first nnz(B) are B's rows
+ *   B_val       device, `capacity` values of the plan's dtype
+ *   capacity    entries B_row_idx / B_val hold; must be >= sum_i nnz(A_i)
+ *               (spkadd_info.nnz_in), else SPKADD_ERR_INVALID_ARG.  Entries
+ *               past nnz(B) are left unspecified.
+ *   nnz_B       host out: nnz(B)
+ * The one-pass kernel runs when every column has s_j <= warp_max (any k);
+ * otherwise the call runs the kernels of spkadd_symbolic and spkadd_numeric
+ * into the same buffers, with the same result (spkadd_info.onepass says
+ * which ran).
+ * Blocks the host twice (class counts after the plan, nnz(B) at the end).
+ * Its device waits are bounded by opt.wait_timeout_ms: when one runs out the
+ * call returns SPKADD_ERR_TIMEOUT and B is not valid.  May be called again;
+ * afterwards the handle is in the state spkadd_numeric leaves it in.
+ */
+spkadd_status spkadd_onepass(spkadd_handle* h, int64_t* B_col_ptr, int32_t* B_row_idx, void* B_val,
+                             int64_t capacity, int64_t* nnz_B);
 
 /*
  * Batches.  Many independent SpKAdd problems B_q = A_q,1 + ... + A_q,k_q
@@ -270,8 +308,11 @@ spkadd_status spkadd_destroy(spkadd_handle* h);
  * Scratch: one fixed array of SPKADD_SCAN_NOALLOC_MAX_N / 4096 + 1 int64
  * (32 KB) defined inside the library; every GPU that loads the library holds
  * it until the process exits.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture.  All calls share the array
+ * array's device address (cudaGetSymbolAddress, with that device current)
+ * and loads the scan kernels' code onto the device; CUDA loads a module's
+ * code lazily and that load takes device memory, so make the first call on
+ * each device at set-up: before the caller's arena claims the device's
+ * memory, and before any stream capture.  Later calls load nothing.  All calls share the array
  * and it keeps the last call's contents; nothing needs to start at zero
  * (every element a call reads, that call wrote first).  Calls that can
  * overlap on the GPU -- on different streams without ordering between them,

@@ -42,7 +42,7 @@ from ._build import LIB_PATH, build  # noqa: F401  (build is re-exported)
 
 __all__ = [
     "SpkaddError", "Options", "Info", "library", "default_options", "spkadd_plan", "spkadd_symbolic",
-    "spkadd_numeric", "spkadd_destroy", "spkadd_get_info", "spkadd_status_string", "spkadd", "Handle",
+    "spkadd_numeric", "spkadd_onepass", "spkadd_destroy", "spkadd_get_info", "spkadd_status_string", "spkadd", "Handle",
     "STATUS", "spkadd_scan_counts_noalloc", "SCAN_NOALLOC_MAX_N", "spkadd_batch_plan", "spkadd_batch_plan_raw",
     "spkadd_batch_symbolic", "spkadd_batch_numeric", "spkadd_batch_numeric_raw", "spkadd_batch", "BatchHandle",
     "SpkaddStream",
@@ -78,13 +78,14 @@ class Options(ctypes.Structure):
                 ("window_max", ctypes.c_int32), ("sort_mode", ctypes.c_int32), ("input_order", ctypes.c_int32),
                 ("block_accumulator", ctypes.c_int32),
                 ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("wait_timeout_ms", ctypes.c_int32), ("test_stall", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "k", "m", "n", "nnz_in", "nnz_out", "cols_warp", "cols_cta", "cols_heavy", "windows", "windows_split",
-        "cols_unique", "workspace_bytes", "kernel_launches", "problems")]
+        "cols_unique", "workspace_bytes", "kernel_launches", "problems", "onepass")]
 
 
 _lib = None
@@ -107,6 +108,8 @@ def library():
         lib.spkadd_symbolic.restype = ctypes.c_int
         lib.spkadd_numeric.argtypes = [P, P, P, P]
         lib.spkadd_numeric.restype = ctypes.c_int
+        lib.spkadd_onepass.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+        lib.spkadd_onepass.restype = ctypes.c_int
         lib.spkadd_get_info.argtypes = [P, ctypes.POINTER(Info)]
         lib.spkadd_get_info.restype = ctypes.c_int
         lib.spkadd_destroy.argtypes = [P]
@@ -160,20 +163,26 @@ _DTYPE = {torch.float32: 0, torch.float64: 1}
 
 
 class Handle:
-    """Owns a spkadd_handle*; keeps the borrowed input tensors alive."""
+    """Owns a spkadd_handle*; keeps the borrowed input tensors alive.
 
-    def __init__(self, ptr, inputs, n, dtype, stream):
+    Every library call on the handle runs with the handle's device current
+    (the C side launches on the current device).
+    """
+
+    def __init__(self, ptr, inputs, n, dtype, stream, device=None):
         self.ptr = ptr
         self.inputs = inputs
         self.n = n
         self.dtype = dtype
         self.stream = stream
+        self.device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.nnz = None
 
     def __del__(self):
         if getattr(self, "ptr", None):
             try:
-                library().spkadd_destroy(self.ptr)
+                with torch.cuda.device(self.device):
+                    library().spkadd_destroy(self.ptr)
             except Exception:
                 pass
             self.ptr = None
@@ -213,34 +222,72 @@ def spkadd_plan(A, m: int, dtype=None, stream=None, options: Options | None = No
     if dtype not in _DTYPE:
         raise TypeError("values must be float32 or float64")
     arr, keep = _csc_array(A, m, dtype)
-    stream, sp = _stream_ptr(stream)
-    h = ctypes.c_void_p()
-    _check(lib.spkadd_plan(ctypes.byref(h), k, arr, _DTYPE[dtype], sp,
-                           ctypes.byref(options) if options is not None else None), "spkadd_plan")
-    return Handle(h, keep, A[0][0].numel() - 1, dtype, stream)
+    dev = A[0][0].device
+    if any(t.device != dev for a in A for t in a):
+        raise TypeError("all inputs must be on one device")
+    with torch.cuda.device(dev):
+        stream, sp = _stream_ptr(stream)
+        h = ctypes.c_void_p()
+        _check(lib.spkadd_plan(ctypes.byref(h), k, arr, _DTYPE[dtype], sp,
+                               ctypes.byref(options) if options is not None else None), "spkadd_plan")
+    return Handle(h, keep, A[0][0].numel() - 1, dtype, stream, dev)
 
 
 def spkadd_symbolic(h: Handle) -> int:
     """spkadd_symbolic: nnz(B(:,j)) per column, their scan, and nnz(B) (blocks once)."""
     nnz = ctypes.c_int64()
-    _check(library().spkadd_symbolic(h.ptr, ctypes.byref(nnz)), "spkadd_symbolic")
+    with torch.cuda.device(h.device):
+        _check(library().spkadd_symbolic(h.ptr, ctypes.byref(nnz)), "spkadd_symbolic")
     h.nnz = int(nnz.value)
     return h.nnz
 
 
 def spkadd_numeric(h: Handle, col_ptr: torch.Tensor, row_idx: torch.Tensor, val: torch.Tensor) -> None:
     """spkadd_numeric: write B into caller-allocated device tensors."""
-    if col_ptr.dtype != torch.int64 or row_idx.dtype != torch.int32 or val.dtype != h.dtype:
-        raise TypeError("B buffers must be int64 col_ptr, int32 row_idx and values of the plan's dtype")
+    dev = h.inputs[0][0].device if h.inputs else None
+    _out_tensor(col_ptr, torch.int64, "col_ptr", dev)
+    _out_tensor(row_idx, torch.int32, "row_idx", dev)
+    _out_tensor(val, h.dtype, "val", dev)
     if col_ptr.numel() != h.n + 1 or (h.nnz is not None and (row_idx.numel() < h.nnz or val.numel() < h.nnz)):
         raise ValueError("B buffers too small")
-    _check(library().spkadd_numeric(h.ptr, col_ptr.data_ptr(), row_idx.data_ptr() if row_idx.numel() else None,
-                                    val.data_ptr() if val.numel() else None), "spkadd_numeric")
+    with torch.cuda.device(h.device):
+        _check(library().spkadd_numeric(h.ptr, col_ptr.data_ptr(), row_idx.data_ptr() if row_idx.numel() else None,
+                                        val.data_ptr() if val.numel() else None), "spkadd_numeric")
+
+
+def _out_tensor(t: torch.Tensor, dtype, what: str, device) -> None:
+    """Output buffers are written as n consecutive elements: require exactly that."""
+    if t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous {dtype} CUDA tensor")
+    if device is not None and t.device != device:
+        raise TypeError(f"{what} must be on {device}")
+
+
+def spkadd_onepass(h: Handle, col_ptr: torch.Tensor, row_idx: torch.Tensor, val: torch.Tensor) -> int:
+    """spkadd_onepass: B in one pass over the inputs into buffers of at least sum nnz(A_i) entries.
+
+    Returns nnz(B); the first nnz(B) entries of row_idx / val are B's.
+    """
+    dev = h.inputs[0][0].device if h.inputs else None
+    _out_tensor(col_ptr, torch.int64, "col_ptr", dev)
+    _out_tensor(row_idx, torch.int32, "row_idx", dev)
+    _out_tensor(val, h.dtype, "val", dev)
+    if col_ptr.numel() != h.n + 1:
+        raise ValueError("col_ptr must hold n + 1 entries")
+    cap = min(row_idx.numel(), val.numel())
+    nnz = ctypes.c_int64()
+    with torch.cuda.device(h.device):
+        _check(library().spkadd_onepass(h.ptr, col_ptr.data_ptr(), row_idx.data_ptr() if row_idx.numel() else None,
+                                        val.data_ptr() if val.numel() else None, cap, ctypes.byref(nnz)),
+               "spkadd_onepass")
+    h.nnz = int(nnz.value)
+    return h.nnz
 
 
 def spkadd_get_info(h: Handle) -> dict:
     info = Info()
-    st = library().spkadd_get_info(h.ptr, ctypes.byref(info))
+    with torch.cuda.device(h.device):
+        st = library().spkadd_get_info(h.ptr, ctypes.byref(info))
     d = {name: int(getattr(info, name)) for name, _ in Info._fields_}
     d["status"] = STATUS.get(st, st)
     return d
@@ -249,19 +296,35 @@ def spkadd_get_info(h: Handle) -> dict:
 def spkadd_destroy(h: Handle) -> None:
     if h.ptr:
         ptr, h.ptr = h.ptr, None
-        _check(library().spkadd_destroy(ptr), "spkadd_destroy")
+        with torch.cuda.device(h.device):
+            _check(library().spkadd_destroy(ptr), "spkadd_destroy")
 
 
-def spkadd(A, m: int, dtype=None, stream=None, options: Options | None = None, info: bool = False):
-    """B = sum of the inputs; returns (col_ptr int64, row_idx int32, val) CUDA tensors."""
+def spkadd(A, m: int, dtype=None, stream=None, options: Options | None = None, info: bool = False,
+           method: str = "onepass"):
+    """B = sum of the inputs; returns (col_ptr int64, row_idx int32, val) CUDA tensors.
+
+    method "onepass": spkadd_onepass into buffers of sum nnz(A_i) entries
+    (row_idx / val are views of their first nnz(B) entries); "twopass":
+    spkadd_symbolic, then exact-size buffers and spkadd_numeric.
+    """
+    if method not in ("onepass", "twopass"):
+        raise ValueError("method must be 'onepass' or 'twopass'")
     h = spkadd_plan(A, m, dtype=dtype, stream=stream, options=options)
     try:
-        nnz = spkadd_symbolic(h)
         dev = A[0][0].device
         col_ptr = torch.empty(h.n + 1, dtype=torch.int64, device=dev)
-        row_idx = torch.empty(nnz, dtype=torch.int32, device=dev)
-        val = torch.empty(nnz, dtype=h.dtype, device=dev)
-        spkadd_numeric(h, col_ptr, row_idx, val)
+        if method == "onepass":
+            cap = sum(a[1].numel() for a in A)
+            row_idx = torch.empty(cap, dtype=torch.int32, device=dev)
+            val = torch.empty(cap, dtype=h.dtype, device=dev)
+            nnz = spkadd_onepass(h, col_ptr, row_idx, val)
+            row_idx, val = row_idx[:nnz], val[:nnz]
+        else:
+            nnz = spkadd_symbolic(h)
+            row_idx = torch.empty(nnz, dtype=torch.int32, device=dev)
+            val = torch.empty(nnz, dtype=h.dtype, device=dev)
+            spkadd_numeric(h, col_ptr, row_idx, val)
         stats = spkadd_get_info(h) if info else None
     finally:
         spkadd_destroy(h)
@@ -279,11 +342,13 @@ def spkadd_scan_counts_noalloc(counts: torch.Tensor, col_ptr: torch.Tensor, stre
     """
     if counts.dtype != torch.int32 or not counts.is_cuda or not counts.is_contiguous():
         raise TypeError("counts must be a contiguous int32 CUDA tensor")
-    if col_ptr.dtype != torch.int64 or not col_ptr.is_cuda or col_ptr.numel() != counts.numel() + 1:
+    _out_tensor(col_ptr, torch.int64, "col_ptr", counts.device)
+    if col_ptr.numel() != counts.numel() + 1:
         raise TypeError("col_ptr must be an int64 CUDA tensor with len(counts) + 1 elements")
-    _, sp = _stream_ptr(stream)
-    _check(library().spkadd_scan_counts_noalloc(counts.data_ptr() if counts.numel() else None, counts.numel(),
-                                                col_ptr.data_ptr(), sp), "spkadd_scan_counts_noalloc")
+    with torch.cuda.device(counts.device):
+        _, sp = _stream_ptr(stream)
+        _check(library().spkadd_scan_counts_noalloc(counts.data_ptr() if counts.numel() else None, counts.numel(),
+                                                    col_ptr.data_ptr(), sp), "spkadd_scan_counts_noalloc")
 
 
 # ---------------------------------------------------------------------------
@@ -297,19 +362,20 @@ assert _CSC_NP.itemsize == ctypes.sizeof(CSC)
 class BatchHandle(Handle):
     """A spkadd_handle* of a batch; n and dtype are per-problem lists."""
 
-    def __init__(self, ptr, inputs, ns, dtypes, stream):
-        super().__init__(ptr, inputs, ns, dtypes, stream)
+    def __init__(self, ptr, inputs, ns, dtypes, stream, device=None):
+        super().__init__(ptr, inputs, ns, dtypes, stream, device)
 
 
 def spkadd_batch_plan_raw(k, m, n, nnz, col_ptr, row_idx, val, dtypes, stream=None,
-                          options: Options | None = None, keep=None) -> BatchHandle:
+                          options: Options | None = None, keep=None, device=None) -> BatchHandle:
     """spkadd_batch_plan from flat descriptor arrays.
 
     k: per-problem input counts (count entries); m, n: per-problem shapes
     (count entries); nnz, col_ptr, row_idx, val: per-input nnz and device
     addresses (sum(k) entries, problem by problem); dtypes: per-problem
     torch.float32 / torch.float64.  `keep` is held by the handle so that the
-    buffers behind the addresses outlive it.
+    buffers behind the addresses outlive it.  The addresses must be memory
+    of `device` (default: the current device).
     """
     lib = library()
     k = np.ascontiguousarray(k, dtype=np.int32)
@@ -328,11 +394,13 @@ def spkadd_batch_plan_raw(k, m, n, nnz, col_ptr, row_idx, val, dtypes, stream=No
     starts = np.concatenate([[0], np.cumsum(k)[:-1]]).astype(np.uint64)
     ptrs = (np.uint64(desc.ctypes.data) + starts * np.uint64(_CSC_NP.itemsize)).astype(np.uint64)
     codes = np.asarray([_DTYPE[d] for d in dtypes], dtype=np.int32)
-    stream, sp = _stream_ptr(stream)
-    h = ctypes.c_void_p()
-    _check(lib.spkadd_batch_plan(ctypes.byref(h), count, k.ctypes.data, ptrs.ctypes.data, codes.ctypes.data, sp,
-                                 ctypes.byref(options) if options is not None else None), "spkadd_batch_plan")
-    return BatchHandle(h, keep, [int(x) for x in n], list(dtypes), stream)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        stream, sp = _stream_ptr(stream)
+        h = ctypes.c_void_p()
+        _check(lib.spkadd_batch_plan(ctypes.byref(h), count, k.ctypes.data, ptrs.ctypes.data, codes.ctypes.data, sp,
+                                     ctypes.byref(options) if options is not None else None), "spkadd_batch_plan")
+    return BatchHandle(h, keep, [int(x) for x in n], list(dtypes), stream, dev)
 
 
 def spkadd_batch_plan(problems, stream=None, options: Options | None = None) -> BatchHandle:
@@ -359,14 +427,19 @@ def spkadd_batch_plan(problems, stream=None, options: Options | None = None) -> 
             ris.append(ri.data_ptr() if ri.numel() else 0)
             vas.append(va.data_ptr() if va.numel() else 0)
         keep.append(A)
-    return spkadd_batch_plan_raw(ks, ms, ns, nnz, cps, ris, vas, dts, stream=stream, options=options, keep=keep)
+    dev = problems[0][0][0][0].device
+    if any(t.device != dev for A, _ in problems for a in A for t in a):
+        raise TypeError("all problems must be on one device")
+    return spkadd_batch_plan_raw(ks, ms, ns, nnz, cps, ris, vas, dts, stream=stream, options=options, keep=keep,
+                                 device=dev)
 
 
 def spkadd_batch_symbolic(h: BatchHandle) -> list:
     """spkadd_batch_symbolic: nnz(B_q) for every problem (blocks once)."""
     count = len(h.n)
     out = np.zeros(count, dtype=np.int64)
-    _check(library().spkadd_batch_symbolic(h.ptr, out.ctypes.data), "spkadd_batch_symbolic")
+    with torch.cuda.device(h.device):
+        _check(library().spkadd_batch_symbolic(h.ptr, out.ctypes.data), "spkadd_batch_symbolic")
     h.nnz = [int(x) for x in out]
     return h.nnz
 
@@ -380,15 +453,17 @@ def spkadd_batch_numeric(h: BatchHandle, outs) -> None:
     ri = np.zeros(count, dtype=np.uint64)
     va = np.zeros(count, dtype=np.uint64)
     for q, (c, r, v) in enumerate(outs):
-        if c.dtype != torch.int64 or r.dtype != torch.int32 or v.dtype != h.dtype[q]:
-            raise TypeError(f"problem {q}: B buffers must be int64, int32 and the problem's dtype")
+        _out_tensor(c, torch.int64, f"problem {q} col_ptr", h.device)
+        _out_tensor(r, torch.int32, f"problem {q} row_idx", h.device)
+        _out_tensor(v, h.dtype[q], f"problem {q} val", h.device)
         if c.numel() != h.n[q] + 1 or (h.nnz is not None and (r.numel() < h.nnz[q] or v.numel() < h.nnz[q])):
             raise ValueError(f"problem {q}: B buffers too small")
         cp[q] = c.data_ptr()
         ri[q] = r.data_ptr() if r.numel() else 0
         va[q] = v.data_ptr() if v.numel() else 0
-    _check(library().spkadd_batch_numeric(h.ptr, cp.ctypes.data, ri.ctypes.data, va.ctypes.data),
-           "spkadd_batch_numeric")
+    with torch.cuda.device(h.device):
+        _check(library().spkadd_batch_numeric(h.ptr, cp.ctypes.data, ri.ctypes.data, va.ctypes.data),
+               "spkadd_batch_numeric")
 
 
 def spkadd_batch_numeric_raw(h: BatchHandle, col_ptr, row_idx, val) -> None:
@@ -403,8 +478,9 @@ def spkadd_batch_numeric_raw(h: BatchHandle, col_ptr, row_idx, val) -> None:
     va = np.ascontiguousarray(val, dtype=np.uint64)
     if not (cp.size == ri.size == va.size == count):
         raise ValueError("one address per problem in each array")
-    _check(library().spkadd_batch_numeric(h.ptr, cp.ctypes.data, ri.ctypes.data, va.ctypes.data),
-           "spkadd_batch_numeric")
+    with torch.cuda.device(h.device):
+        _check(library().spkadd_batch_numeric(h.ptr, cp.ctypes.data, ri.ctypes.data, va.ctypes.data),
+               "spkadd_batch_numeric")
 
 
 def spkadd_batch(problems, stream=None, options: Options | None = None, info: bool = False):
@@ -433,23 +509,29 @@ class SpkaddStream:
     until the next add (their numeric work may still be running).
     """
 
-    def __init__(self, m: int, n: int, dtype=torch.float64, stream=None, options: Options | None = None):
+    def __init__(self, m: int, n: int, dtype=torch.float64, stream=None, options: Options | None = None,
+                 device=None):
         if dtype not in _DTYPE:
             raise TypeError("values must be float32 or float64")
         self.m, self.n, self.dtype = int(m), int(n), dtype
-        self.stream, sp = _stream_ptr(stream)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.ptr = ctypes.c_void_p()
         self._keep = None
-        _check(library().spkadd_stream_create(ctypes.byref(self.ptr), self.m, self.n, _DTYPE[dtype], sp,
-                                              ctypes.byref(options) if options is not None else None),
-               "spkadd_stream_create")
+        with torch.cuda.device(self.device):
+            self.stream, sp = _stream_ptr(stream)
+            _check(library().spkadd_stream_create(ctypes.byref(self.ptr), self.m, self.n, _DTYPE[dtype], sp,
+                                                  ctypes.byref(options) if options is not None else None),
+                   "spkadd_stream_create")
 
     def add(self, A) -> int:
         """B <- B + sum(A); returns nnz(B)."""
         if len(A) == 0:
             _check(1, "spkadd_stream_add")
         arr, keep = _csc_array(A, self.m, self.dtype)
-        _check(library().spkadd_stream_add(self.ptr, len(A), arr), "spkadd_stream_add")
+        if any(t.device != self.device for a in A for t in a):
+            raise TypeError(f"inputs must be on {self.device}")
+        with torch.cuda.device(self.device):
+            _check(library().spkadd_stream_add(self.ptr, len(A), arr), "spkadd_stream_add")
         self._keep = keep
         return self.nnz
 
@@ -466,19 +548,20 @@ class SpkaddStream:
     def result(self):
         """B as (col_ptr int64, row_idx int32, val) CUDA tensors (copies)."""
         nnz = self.nnz
-        dev = torch.device("cuda", torch.cuda.current_device())
-        with torch.cuda.stream(self.stream):
+        dev = self.device
+        with torch.cuda.device(dev), torch.cuda.stream(self.stream):
             cp = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
             ri = torch.empty(nnz, dtype=torch.int32, device=dev)
             va = torch.empty(nnz, dtype=self.dtype, device=dev)
-        _check(library().spkadd_stream_result(self.ptr, cp.data_ptr(), ri.data_ptr() if nnz else None,
-                                              va.data_ptr() if nnz else None), "spkadd_stream_result")
+            _check(library().spkadd_stream_result(self.ptr, cp.data_ptr(), ri.data_ptr() if nnz else None,
+                                                  va.data_ptr() if nnz else None), "spkadd_stream_result")
         return cp, ri, va
 
     def close(self) -> None:
         if getattr(self, "ptr", None):
             ptr, self.ptr = self.ptr, None
-            _check(library().spkadd_stream_destroy(ptr), "spkadd_stream_destroy")
+            with torch.cuda.device(self.device):
+                _check(library().spkadd_stream_destroy(ptr), "spkadd_stream_destroy")
         self._keep = None
 
     def __del__(self):

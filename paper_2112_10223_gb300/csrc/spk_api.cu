@@ -87,6 +87,7 @@ spkadd_status from_device_err(int32_t err) {
   if (err & spk::ERR_OVERFLOW) return SPKADD_ERR_OVERFLOW;
   if (err & spk::ERR_RANGE) return SPKADD_ERR_INDEX_RANGE;
   if (err & spk::ERR_UNSORTED) return SPKADD_ERR_UNSORTED;
+  if (err & spk::ERR_TIMEOUT) return SPKADD_ERR_TIMEOUT;
   if (err & (spk::ERR_WINDOW_CAP | spk::ERR_INTERNAL)) return SPKADD_ERR_INTERNAL;
   return SPKADD_OK;
 }
@@ -142,6 +143,8 @@ struct spkadd_handle {
   Counters* d_ctr = nullptr;
   int64_t* d_colptr = nullptr;
   long long* d_scan = nullptr;
+  char* d_op = nullptr;                // one-pass: ticket counter and look-back words
+  bool onepass = false;                // B last computed by the one-pass kernel
   int32_t* d_offs = nullptr;
   Counters h_ctr{};
   int64_t nnz_out = -1;
@@ -163,6 +166,8 @@ SPK_API void spkadd_default_options(spkadd_options* opt) {
   opt->sort_mode = 0;
   opt->input_order = 0;
   opt->block_accumulator = 0;
+  opt->wait_timeout_ms = 2000;
+  opt->test_stall = 0;
 }
 
 SPK_API const char* spkadd_status_string(spkadd_status s) {
@@ -193,6 +198,8 @@ static spkadd_status check_options(const spkadd_options& o) {
   if (o.input_order != 0 && o.input_order != 1) return SPKADD_ERR_INVALID_ARG;
   if (o.block_accumulator < 0 || o.block_accumulator > 2) return SPKADD_ERR_INVALID_ARG;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SPKADD_ERR_INVALID_ARG;
+  if (o.wait_timeout_ms < 1 || o.wait_timeout_ms > 600000) return SPKADD_ERR_INVALID_ARG;
+  if (o.test_stall != 0 && o.test_stall != 1) return SPKADD_ERR_INVALID_ARG;
   return SPKADD_OK;
 }
 
@@ -297,6 +304,7 @@ static spkadd_status plan_problems(spkadd_handle** hp, bool batch, int count, co
   const size_t o_srch = cv.take<int32_t>(win_cap);
   const size_t o_colp = cv.take<int64_t>(ncols + 1);
   const size_t o_scan = cv.take<long long>(spk::scan_tiles(ncols));
+  const size_t o_op = cv.take<char>(batch ? 0 : spk::onepass_scratch_bytes(ncols));
   h->ws_bytes = align_up(cv.off, 256);
   h->ws = static_cast<char*>(h->dev_alloc(h->ws_bytes));
   if (!h->ws) {
@@ -317,6 +325,7 @@ static spkadd_status plan_problems(spkadd_handle** hp, bool batch, int count, co
   h->d_search = reinterpret_cast<int32_t*>(h->ws + o_srch);
   h->d_colptr = reinterpret_cast<int64_t*>(h->ws + o_colp);
   h->d_scan = reinterpret_cast<long long*>(h->ws + o_scan);
+  h->d_op = batch ? nullptr : h->ws + o_op;
 
   // Problem and pointer tables plus zeroed counters: one host staging
   // buffer, one copy.
@@ -516,6 +525,7 @@ SPK_API spkadd_status spkadd_numeric(spkadd_handle* h, int64_t* B_col_ptr, int32
   cudaError_t ce = cudaMemcpyAsync(B_col_ptr, h->d_colptr, (size_t)(h->ncols + 1) * sizeof(int64_t),
                                    cudaMemcpyDeviceToDevice, h->st);
   if (ce != cudaSuccess) return from_cuda(ce);
+  h->onepass = false;
   spk::Outs out{};
   out.row0 = B_row_idx;
   out.val0 = B_val;
@@ -523,6 +533,58 @@ SPK_API spkadd_status spkadd_numeric(spkadd_handle* h, int64_t* B_col_ptr, int32
   const spkadd_status s = run_numeric(h, out);
   if (s != SPKADD_OK) return s;
   h->state = ST_NUMERIC;
+  return SPKADD_OK;
+}
+
+// One pass over the inputs (symbolic count, scan by decoupled look-back and
+// numeric sum fused) into buffers sized by sum_i nnz(A_i); the phases of
+// spkadd_symbolic / spkadd_numeric when the problem does not qualify.
+SPK_API spkadd_status spkadd_onepass(spkadd_handle* h, int64_t* B_col_ptr, int32_t* B_row_idx, void* B_val,
+                                     int64_t capacity, int64_t* nnz_B) {
+  if (!h || !B_col_ptr || !nnz_B || h->batch) return SPKADD_ERR_INVALID_ARG;
+  if (h->state < ST_PLANNED) return SPKADD_ERR_STATE;
+  if (capacity < h->nnz_in) return SPKADD_ERR_INVALID_ARG;
+  if (h->nnz_in > 0 && (!B_row_idx || !B_val)) return SPKADD_ERR_INVALID_ARG;
+  Pinned* pb = pinned_block();
+  if (!pb) return SPKADD_ERR_NOMEM;
+  cudaError_t ce = cudaMemcpyAsync(&pb->ctr, h->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, h->st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->st);
+  if (ce != cudaSuccess) return from_cuda(ce);
+  spkadd_status ds = from_device_err(pb->ctr.err);
+  if (ds != SPKADD_OK) return ds;
+  const Counters c = pb->ctr;
+  const bool fits = h->ncols > 0 && c.n_cta == 0 && c.n_heavy == 0 && h->dt_mode != 2;
+  if (!fits) {
+    h->onepass = false;
+    spkadd_status s = SPKADD_OK;
+    if (h->state < ST_SYMBOLIC) s = run_symbolic(h);
+    if (s != SPKADD_OK) return s;
+    s = spkadd_numeric(h, B_col_ptr, B_row_idx, B_val);
+    if (s != SPKADD_OK) return s;
+    *nnz_B = h->nnz_out;
+    return SPKADD_OK;
+  }
+  h->h_ctr = c;
+  int grid = 0;
+  ce = cudaMemsetAsync(&h->d_ctr->n_unique, 0, sizeof(int32_t), h->st);
+  if (ce != cudaSuccess) return from_cuda(ce);
+  ce = spk::launch_onepass(h->in, h->dt_mode, h->d_s, (int)h->ncols, h->opt.warp_max, B_col_ptr,
+                           B_row_idx, B_val, capacity, h->d_op, h->opt.sort_mode == 1, h->opt.test_stall,
+                           (unsigned long long)h->opt.wait_timeout_ms * 1000000ull, h->d_ctr, h->dev, h->st, &grid);
+  if (ce != cudaSuccess) return from_cuda(ce);
+  h->launches += grid > 0 ? 1 : 0;
+  ce = cudaMemcpyAsync(&pb->ctr, h->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, h->st);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(&pb->nnz, B_col_ptr + h->ncols, sizeof(long long), cudaMemcpyDeviceToHost, h->st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->st);
+  if (ce != cudaSuccess) return from_cuda(ce);
+  h->h_ctr = pb->ctr;
+  ds = from_device_err(pb->ctr.err);
+  if (ds != SPKADD_OK) return ds;
+  h->nnz_out = pb->nnz;
+  h->onepass = true;
+  h->state = ST_NUMERIC;
+  *nnz_B = h->nnz_out;
   return SPKADD_OK;
 }
 
@@ -584,6 +646,7 @@ SPK_API spkadd_status spkadd_get_info(spkadd_handle* h, spkadd_info* info) {
   info->cols_unique = c.n_unique;
   info->workspace_bytes = (int64_t)(h->ws_bytes + h->offs_bytes);
   info->kernel_launches = h->launches;
+  info->onepass = h->onepass ? 1 : 0;
   return from_device_err(c.err);
 }
 

@@ -20,6 +20,7 @@ enum : int32_t {
   ERR_RANGE = 4,         // validate: row outside [0, m) or bad col_ptr
   ERR_WINDOW_CAP = 8,    // more row windows than the workspace holds
   ERR_INTERNAL = 16,     // a size invariant failed (bug guard; work skipped)
+  ERR_TIMEOUT = 32,      // a bounded device-side wait gave up
 };
 
 // One thread-block work item of the numeric pass: a whole CTA-class column

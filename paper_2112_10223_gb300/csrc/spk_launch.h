@@ -36,6 +36,8 @@ cudaError_t launch_col_inst(const Inputs& in, int32_t* col_inst, int sms, cudaSt
 cudaError_t launch_validate(const Inputs& in, const int64_t* nnz, Counters* ctr, int sms, cudaStream_t st);
 size_t scan_tiles(int64_t n);
 cudaError_t launch_scan(const int32_t* u, int n, long long* tile_buf, int64_t* col_ptr, cudaStream_t st);
+// Loads the scan kernels onto the current device (module loading is lazy).
+cudaError_t load_scan_kernels();
 cudaError_t launch_window_search(const Inputs& in, const Window* win, const int32_t* search_list, int n_search,
                                  int32_t* offs, int sms, cudaStream_t st);
 
@@ -63,5 +65,15 @@ cudaError_t launch_out_colptr(const Inputs& in, const Outs& o, const int64_t* co
 cudaError_t launch_colptr_narrow(const int64_t* src, int32_t* dst, int64_t n1, int sms, cudaStream_t st);
 cudaError_t launch_colptr_widen(const int32_t* src, int64_t* dst, int64_t n1, int sms, cudaStream_t st);
 cudaError_t launch_inst_nnz(const Inputs& in, const int64_t* col_ptr, int64_t* nnz, cudaStream_t st);
+
+// One-pass path (one problem, every column s_j <= warp_max): B written into
+// buffers of `capacity` entries; `scratch` holds onepass_scratch_bytes(n)
+// bytes (ticket counter and look-back words).
+int onepass_tile_cols();
+size_t onepass_scratch_bytes(int64_t ncols);
+cudaError_t launch_onepass(const Inputs& in, int dt, const int32_t* s, int n, int warp_max, int64_t* col_ptr,
+                           int32_t* out_row, void* out_val, long long capacity, void* scratch, int force_dedup,
+                           int debug_stall, unsigned long long wait_ns, Counters* ctr, const DeviceInfo& dev,
+                           cudaStream_t st, int* grid_out);
 
 }  // namespace spk

@@ -23,7 +23,9 @@ bool g_have[64];
 
 // Device address of g_scan_scratch on the current device, looked up once per
 // device.  In host code the name g_scan_scratch is only a host-side stand-in,
-// so kernels must be given this address instead.
+// so kernels must be given this address instead.  The same first call loads
+// the scan kernels' code onto the device (CUDA loads modules lazily, and a
+// load takes device memory), so later calls load nothing.
 cudaError_t scratch_address(long long** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -33,6 +35,7 @@ cudaError_t scratch_address(long long** out) {
   if (!g_have[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scan_scratch);
+    if (e == cudaSuccess) e = spk::load_scan_kernels();
     if (e != cudaSuccess) return e;
     g_addr[dev] = static_cast<long long*>(p);
     g_have[dev] = true;

@@ -272,6 +272,18 @@ cudaError_t launch_validate(const Inputs& in, const int64_t* nnz, Counters* ctr,
 
 size_t scan_tiles(int64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 1; }
 
+// Loads the scan kernels' code onto the current device now (CUDA loads
+// modules lazily, at a kernel's first launch, and loading takes device
+// memory); a caller that must not allocate during later calls runs this once
+// at set-up.
+cudaError_t load_scan_kernels() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_scan_tiles);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_scan_sums);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_scan_apply);
+  return e;
+}
+
 cudaError_t launch_scan(const int32_t* u, int n, long long* tile_buf, int64_t* col_ptr, cudaStream_t st) {
   const int tiles = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
   long long* grand = tile_buf + tiles;

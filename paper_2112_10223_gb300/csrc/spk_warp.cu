@@ -30,6 +30,8 @@
 
 #include "spk_common.cuh"
 #include "spk_launch.h"
+#include "spk_lookback.cuh"
+
 
 namespace spk {
 
@@ -248,6 +250,22 @@ struct BucketCount {  // pass 1: entries per order-preserving bucket
   __device__ __forceinline__ void post(uint32_t, int32_t, V, bool, int) {}
 };
 
+template <typename V>
+struct BucketCountChecked {  // pass 1 of the one-pass kernel: rows outside [0, m) are flagged, never counted
+  uint32_t* cnt;
+  uint32_t mul;
+  uint32_t m;
+  bool bad;
+  __device__ __forceinline__ uint32_t pre(int32_t r, V, bool ok, int) {
+    if (ok) {
+      if ((uint32_t)r < m) atomicAdd(&cnt[pad16((int)bucket_hi(r, mul))], 1u);
+      else bad = true;
+    }
+    return 0u;
+  }
+  __device__ __forceinline__ void post(uint32_t, int32_t, V, bool, int) {}
+};
+
 template <typename V, bool NUMERIC>
 struct BucketFile {  // pass 2: file the row (and value) at the bucket's next slot
   uint32_t* cnt;
@@ -308,7 +326,7 @@ struct FilterMark {
 // Repeated rows of the column, -1 when the marks overflow (then the caller
 // runs the bucket path), or -2 when a row lies outside [0, m) (the bucket
 // passes index their counters by row and are never run on such a column).
-// Leaves the filter zero.
+// Leaves the filter zero on all three outcomes.
 template <int U>
 __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, int off, int j, bool resident, int rbeg,
                                                      int rlen, const int32_t* my_ri, int s, const int* m_ptr,
@@ -332,7 +350,12 @@ __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, in
     const int32_t x = e < s ? stage[e] : INT32_MAX;
     v[q] = x & INT32_MAX;
     if (e < s) {
-      filt[filter_hash(v[q]) >> 5] = 0u;  // clear the filter for the next column
+      // Clear the filter for the next column: the word of the row as staged
+      // (mark bit dropped) and, for a staged value with bit 31 set, also the
+      // word of that value itself (a negative input row, which is flagged
+      // below), so the filter is left zero on every path.
+      filt[filter_hash(v[q]) >> 5] = 0u;
+      if (x < 0) filt[filter_hash(x) >> 5] = 0u;
       if (x < 0) mine |= 1u << q;
       top = max(top, (uint32_t)v[q]);
     }
@@ -395,7 +418,7 @@ __device__ __forceinline__ int bucket_scan(uint32_t* cnt, uint32_t* mlist, int N
 // Insertion sort of the listed multi-entry buckets, one bucket per lane (they
 // hold 2-3 entries mostly).  Returns this lane's count of repeated rows met
 // (the symbolic count uses it).
-template <typename V, bool NUMERIC>
+template <typename V, bool NUMERIC, bool COUNT = !NUMERIC>
 __device__ __forceinline__ int sort_buckets(int32_t* skey, V* sval, const uint32_t* mlist, int nmulti, int lane) {
   int dups = 0;
   for (int i = lane; i < nmulti; i += 32) {
@@ -414,7 +437,7 @@ __device__ __forceinline__ int sort_buckets(int32_t* skey, V* sval, const uint32
       skey[y + 1] = kx;
       if constexpr (NUMERIC) sval[y + 1] = vx;
     }
-    if constexpr (!NUMERIC)
+    if constexpr (COUNT)
       for (int x = lo + 1; x < hi; ++x) dups += skey[x] == skey[x - 1];
   }
   return dups;
@@ -605,6 +628,162 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_col(Inputs in, WarpColAr
 }
 
 // ---------------------------------------------------------------------------
+// One pass over the inputs (spkadd_onepass).  Sec. II-D's symbolic phase exists
+// so that B can be allocated before the numeric phase; here B goes into
+// buffers sized by nnz(B) <= sum_i nnz(A_i) (Sec. II-A), and each column's
+// offset comes from a decoupled look-back over tiles of WARPS consecutive
+// columns, so no pass reads the rows only to count them.  A block takes a
+// tile from a ticket counter (tiles start in ticket order, which the
+// look-back needs); each warp runs the numeric passes above on its column,
+// counts the repeated rows its bucket sorts meet (nnz(B(:,j)) = s_j minus
+// them: Alg. 6's count), and once warp 0 has the tile's offset writes B(:,j).
+// ---------------------------------------------------------------------------
+struct OnepassArgs {
+  const int32_t* s_arr;        // s_j (plan)
+  int64_t* col_ptr;            // B: n + 1 int64
+  int32_t* out_row;            // B: `capacity` rows
+  void* out_val;               // B: `capacity` values
+  long long capacity;
+  unsigned int* queue;         // tile ticket counter, zero at launch
+  unsigned long long* status;  // look-back words, one per tile, zero at launch
+  Counters* ctr_w;
+  int n;
+  int ntiles;
+  int smax;
+  int force_dedup;
+  int debug_stall;             // test switch: tile 1's look-back also waits on a word nothing writes
+  unsigned long long wait_ns;  // bound of every device-side wait
+};
+
+template <int WARPS>
+struct OnepassTile {
+  int ticket;
+  int bad;                     // the look-back gave up
+  long long off;               // the tile's first entry in B
+  int u[2][WARPS];             // nnz(B(:,j)) of the tile's columns, by iteration parity
+  int uq[WARPS];               // 1: column without repeated rows
+};
+
+template <int DT, bool RES, int WARPS, int U>
+__global__ void __launch_bounds__(WARPS * 32, 3) k_warp_onepass(Inputs in, OnepassArgs a) {
+  using VB = typename std::conditional<DT == 1, double, float>::type;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ OnepassTile<WARPS> T;
+  __shared__ uint32_t s_mul[16];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int smax = a.smax;
+  unsigned char* base = sm_raw + (size_t)wid * warp_col_bytes<VB, true>(smax);
+  VB* sval = reinterpret_cast<VB*>(base);
+  int32_t* skey = reinterpret_cast<int32_t*>(base + (size_t)smax * sizeof(VB));
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(skey + smax);
+  uint32_t* mlist = cnt + padded_words(smax);
+  if (threadIdx.x < 16) s_mul[threadIdx.x] = in.inst[0].bucket_mul[threadIdx.x];
+  const int k = in.inst[0].k;
+  const uint32_t m = (uint32_t)in.inst[0].m;
+  if (RES && k > 32) {  // the host never launches this; never index lanes past k
+    if (threadIdx.x == 0) atomicOr(&a.ctr_w->err, ERR_INTERNAL);
+    return;
+  }
+  const int32_t* my_cp = nullptr;
+  const int32_t* my_ri = nullptr;
+  const VB* my_va = nullptr;
+  if (RES && lane < k) {
+    my_cp = in.cp[lane];
+    my_ri = in.ri[lane];
+    my_va = static_cast<const VB*>(in.val[lane]);
+  }
+  for (int it = 0;; ++it) {
+    if (threadIdx.x == 0) T.ticket = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int tile = T.ticket;
+    if (tile >= a.ntiles) break;
+    int* tu = T.u[it & 1];
+    const int j = tile * WARPS + wid;
+    const bool live = j < a.n;
+    int beg = 0, len = 0, s = 0;
+    if (live) {
+      if (RES) {
+        if (lane < k) {
+          beg = __ldg(my_cp + j);
+          len = __ldg(my_cp + j + 1) - beg;
+        }
+        s = warp_sum(len);
+      } else {
+        s = __ldg(a.s_arr + j);
+      }
+    }
+    int dups = 0;
+    bool bad = false;
+    if (s > 0) {
+      const int qb = max(5, ceil_log2(s));
+      const int NB = 1 << qb;
+      if (NB > smax) {  // not reachable when every column is light
+        if (lane == 0) atomicOr(&a.ctr_w->err, ERR_INTERNAL);
+        bad = true;
+      } else {
+        const uint32_t mul = s_mul[qb];
+        for (int b = lane; b < padded_words(NB); b += 32) cnt[b] = 0u;
+        __syncwarp();
+        // Pass 1: entries per bucket; rows outside [0, m) are flagged.
+        BucketCountChecked<VB> count{cnt, mul, m, false};
+        ChunkCache cc{{0, 0}, {0, 0}, false};
+        for_each_column_entry<false, U, VB>(in, k, 0, j, RES, beg, len, my_ri, my_va, lane, count, cc);
+        bad = __any_sync(SPK_FULL, count.bad);
+        if (!bad) {
+          __syncwarp();
+          const int nmulti = bucket_scan(cnt, mlist, NB, lane);
+          __syncwarp();
+          // Pass 2: file every entry at its bucket's next slot.
+          BucketFile<VB, true> file{cnt, skey, sval, mul};
+          for_each_column_entry<true, U, VB>(in, k, 0, j, RES, beg, len, my_ri, my_va, lane, file, cc);
+          __syncwarp();
+          dups = warp_sum(sort_buckets<VB, true, true>(skey, sval, mlist, nmulti, lane));
+          __syncwarp();
+        } else if (lane == 0) {
+          atomicOr(&a.ctr_w->err, ERR_RANGE);  // B is not computed for such a column
+        }
+      }
+    }
+    const int u = (s > 0 && !bad) ? s - dups : 0;
+    if (lane == 0) {
+      tu[wid] = u;
+      T.uq[wid] = (s > 0 && !bad && dups == 0) ? 1 : 0;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      long long agg = lane < WARPS ? tu[lane] : 0;
+      agg = lb_warp_sum64(agg);
+      bool pois = false;
+      const long long excl = tile_lookback(a.status, tile, agg, a.wait_ns, a.debug_stall && tile == 1, &pois, lane);
+      const int uq = __popc(__ballot_sync(SPK_FULL, lane < WARPS && T.uq[lane < WARPS ? lane : 0]));
+      if (lane == 0) {
+        if (uq) atomicAdd(&a.ctr_w->n_unique, uq);
+        T.off = excl;
+        T.bad = pois ? 1 : 0;
+        if (pois) atomicOr(&a.ctr_w->err, ERR_TIMEOUT);
+      }
+    }
+    __syncthreads();
+    if (live && !T.bad) {
+      long long o = T.off;
+      for (int c = 0; c < wid; ++c) o += tu[c];
+      if (lane == 0) {
+        a.col_ptr[j] = o;
+        if (j == a.n - 1) a.col_ptr[a.n] = o + u;
+      }
+      if (u > 0) {
+        if (o + u <= a.capacity)
+          write_sorted<VB>(skey, sval, s, u, a.force_dedup, a.out_row + o, static_cast<VB*>(a.out_val) + o, a.ctr_w,
+                           lane);
+        else if (lane == 0)
+          atomicOr(&a.ctr_w->err, ERR_INTERNAL);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
 static int pow2_at_least(int x) {
@@ -681,6 +860,58 @@ cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const
   a.only_dtype = 1;
   if (e == cudaSuccess) e = launch_warp_col<1, true>(in, a, warp_max, n_cols, dev, st);
   return e;
+}
+
+template <int DT>
+static cudaError_t launch_onepass_t(const Inputs& in, OnepassArgs a, int warp_max, const DeviceInfo& dev,
+                                    cudaStream_t st, int* grid_out) {
+  using VB = typename std::conditional<DT == 1, double, float>::type;
+  constexpr int WARPS = 8;  // columns per tile (warps per block)
+  constexpr int U = 8;
+  a.smax = pow2_at_least(warp_max) < 32 ? 32 : pow2_at_least(warp_max);
+  const size_t smem = (size_t)WARPS * warp_col_bytes<VB, true>(a.smax);
+  auto kern = in.kmax <= 32 ? k_warp_onepass<DT, true, WARPS, U> : k_warp_onepass<DT, false, WARPS, U>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WARPS * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  int grid = dev.sms * occ;
+  if (grid > a.ntiles) grid = a.ntiles;
+  *grid_out = grid;
+  kern<<<grid, WARPS * 32, smem, st>>>(in, a);
+  return cudaGetLastError();
+}
+
+int onepass_tile_cols() { return 8; }
+
+size_t onepass_scratch_bytes(int64_t ncols) { return 8 + (size_t)((ncols + 7) / 8) * 8 + 8; }
+
+cudaError_t launch_onepass(const Inputs& in, int dt, const int32_t* s, int n, int warp_max, int64_t* col_ptr,
+                           int32_t* out_row, void* out_val, long long capacity, void* scratch, int force_dedup,
+                           int debug_stall, unsigned long long wait_ns, Counters* ctr, const DeviceInfo& dev,
+                           cudaStream_t st, int* grid_out) {
+  *grid_out = 0;
+  if (warp_max < 1 || warp_max > WARP_MAX_LIMIT || in.col_inst) return cudaErrorInvalidValue;
+  OnepassArgs a{};
+  a.s_arr = s;
+  a.col_ptr = col_ptr;
+  a.out_row = out_row;
+  a.out_val = out_val;
+  a.capacity = capacity;
+  a.ctr_w = ctr;
+  a.n = n;
+  a.ntiles = (n + onepass_tile_cols() - 1) / onepass_tile_cols();
+  a.force_dedup = force_dedup;
+  a.debug_stall = debug_stall;
+  a.wait_ns = wait_ns;
+  a.queue = static_cast<unsigned int*>(scratch);
+  a.status = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + 8);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 8 + (size_t)a.ntiles * 8, st);
+  if (e != cudaSuccess || a.ntiles == 0) return e;
+  return dt == 1 ? launch_onepass_t<1>(in, a, warp_max, dev, st, grid_out)
+                 : launch_onepass_t<0>(in, a, warp_max, dev, st, grid_out);
 }
 
 }  // namespace spk

@@ -135,7 +135,7 @@ class Server:
         h = spkadd_batch_plan_raw(k, [r.m for r in reqs], [r.n for r in reqs],
                                   np.concatenate([d["nnz"] for d in desc]), np.concatenate([d["cp"] for d in desc]),
                                   np.concatenate([d["ri"] for d in desc]), np.concatenate([d["va"] for d in desc]),
-                                  [r.dtype for r in reqs], stream=stream, options=self.options)
+                                  [r.dtype for r in reqs], stream=stream, options=self.options, device=self.device)
         nnz = np.asarray(spkadd_batch_symbolic(h), dtype=np.int64)
         n1 = np.asarray([r.n + 1 for r in reqs], dtype=np.int64)
         is64 = np.asarray([r.dtype == torch.float64 for r in reqs])
@@ -182,6 +182,10 @@ class Server:
     # -- a trace ---------------------------------------------------------------
     def run(self, requests) -> ServeStats:
         """Serve `requests` (sorted by arrival, seconds from now) in real time."""
+        with torch.cuda.device(self.device):  # the C library launches on the current device
+            return self._run(requests)
+
+    def _run(self, requests) -> ServeStats:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         queue = collections.deque()
         inflight = collections.deque()

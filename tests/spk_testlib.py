@@ -21,10 +21,10 @@ def to_np(A):
     return [tuple(t.detach().cpu().numpy() for t in a) for a in A]
 
 
-def run_gpu(A, m, dtype=None, options=None, info=False):
+def run_gpu(A, m, dtype=None, options=None, info=False, method="onepass"):
     dev = torch.device("cuda:0")
     Ad = [tuple(t.to(dev) for t in a) for a in A]
-    out = spk.spkadd(Ad, m, dtype=dtype, options=options, info=info)
+    out = spk.spkadd(Ad, m, dtype=dtype, options=options, info=info, method=method)
     torch.cuda.synchronize()
     return out
 

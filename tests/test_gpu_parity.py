@@ -277,31 +277,36 @@ def test_user_allocator_and_allocation_failure():
 
 
 # ---------------------------------------------------------- full-size workloads
-def test_er_k32_2pow20_d16_fp64_sampled():
-    """k = 32 ER 2^20 x 2^20, 16 distinct rows per column, fp64 uniform [-1, 1]; sampled columns vs oracle."""
+def _full_size_every_column(A, m, dtype, methods):
+    """Whole-matrix parity at full size: every column against the oracle (OpenMP over the host's cores)."""
+    want = oracle.add(to_np(A))
+    infos = {}
+    for method in methods:
+        cp, ri, va, info = spk.spkadd(A, m, info=True, method=method)
+        torch.cuda.synchronize()
+        check_global_invariants(A, (cp, ri, va), m)
+        compare((cp.cpu().numpy(), ri.cpu().numpy(), va.cpu().numpy()), want, dtype)
+        infos[method] = info
+        del cp, ri, va
+    return infos
+
+
+def test_er_k32_2pow20_d16_fp64_every_column():
+    """k = 32 ER 2^20 x 2^20, 16 distinct rows per column, fp64 uniform [-1, 1]: every column vs the oracle,
+    through the one-pass kernel and through the symbolic + numeric kernels."""
     dev = torch.device("cuda:0")
     A = synth.er(32, 1 << 20, 1 << 20, 16, seed=0, dtype=F64, device=dev)
-    B, info = None, None
-    cp, ri, va, info = spk.spkadd(A, 1 << 20, info=True)
-    torch.cuda.synchronize()
-    B = (cp, ri, va)
-    assert info["cols_warp"] == 1 << 20
-    check_global_invariants(A, B, 1 << 20)
-    cols, _ = sample_columns(A, 3000, 16, seed=1)
-    check_sampled(A, B, 1 << 20, cols, F64)
+    infos = _full_size_every_column(A, 1 << 20, F64, ("onepass", "twopass"))
+    assert infos["onepass"]["onepass"] == 1 and infos["twopass"]["cols_warp"] == 1 << 20
 
 
-def test_rmat_k64_scale20_fp32_sampled():
-    """k = 64 independent R-MAT scale 20, edge factor 16, (.57, .19, .19, .05), fp32; sampled columns vs oracle."""
+def test_rmat_k64_scale20_fp32_every_column():
+    """k = 64 independent R-MAT scale 20, edge factor 16, (.57, .19, .19, .05), fp32: every column vs the oracle."""
     dev = torch.device("cuda:0")
     A = synth.rmat(64, 20, 16, seed=0, dtype=F32, device=dev)
-    cp, ri, va, info = spk.spkadd(A, 1 << 20, info=True)
-    torch.cuda.synchronize()
-    B = (cp, ri, va)
+    infos = _full_size_every_column(A, 1 << 20, F32, ("twopass",))
+    info = infos["twopass"]
     assert info["cols_heavy"] > 0 and info["windows_split"] > 0
-    check_global_invariants(A, B, 1 << 20)
-    cols, _ = sample_columns(A, 3000, 48, seed=2)
-    check_sampled(A, B, 1 << 20, cols, F32)
 
 
 @pytest.mark.parametrize("dtype,kind", [(F64, "int8"), (F64, "uniform"), (F32, "uniform")])
@@ -522,7 +527,8 @@ def _sorted_columns(cp, ri, va):
 def test_unsorted_output_same_pairs(dtype, kind):
     # m = 2^20: most columns have no repeated row, so they skip the sort
     A = synth.er(32, 1 << 20, 700, 16, seed=41, dtype=dtype, value_kind=kind)
-    cp, ri, va = run_gpu(A, 1 << 20, options=spk.default_options(sort_mode=2))
+    # sort_mode 2 is a mode of the numeric kernel (the one-pass kernel sorts every column)
+    cp, ri, va = run_gpu(A, 1 << 20, options=spk.default_options(sort_mode=2), method="twopass")
     unsorted = any(bool((ri[int(cp[j]) + 1:int(cp[j + 1])] < ri[int(cp[j]):int(cp[j + 1]) - 1]).any())
                    for j in range(700))
     assert unsorted  # the mode really leaves some columns unsorted

@@ -61,3 +61,40 @@ def test_noalloc_scan_rejects_too_many_columns():
     st = lib.spkadd_scan_counts_noalloc(counts.data_ptr(), spk.SCAN_NOALLOC_MAX_N + 1, out.data_ptr(), None)
     assert st == 10  # SPKADD_ERR_UNSUPPORTED, nothing launched
     assert lib.spkadd_scan_counts_noalloc(counts.data_ptr(), -1, out.data_ptr(), None) == 1
+
+
+def test_noalloc_scan_at_the_size_limit_and_empty():
+    """n = SPKADD_SCAN_NOALLOC_MAX_N fills every tile slot of the scratch array (the last holds the total);
+    n = 0 writes the single column pointer 0."""
+    n = spk.SCAN_NOALLOC_MAX_N
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2)
+    counts = torch.randint(0, 64, (n,), generator=g, device="cuda", dtype=torch.int32)
+    want = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    want[1:] = torch.cumsum(counts.to(torch.int64), 0)
+    for _ in range(2):
+        out = torch.full((n + 1,), -1, dtype=torch.int64, device="cuda")
+        spk.spkadd_scan_counts_noalloc(counts, out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, want)
+    del counts, want, out
+    empty = torch.zeros(0, dtype=torch.int32, device="cuda")
+    one = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    spk.spkadd_scan_counts_noalloc(empty, one)
+    torch.cuda.synchronize()
+    assert int(one.item()) == 0
+
+
+def test_noalloc_scan_takes_no_device_memory_after_the_first_call():
+    """After a first call on the device, a further call leaves the device's free memory unchanged."""
+    n = 4096 * 40 + 3
+    counts = torch.ones(n, dtype=torch.int32, device="cuda")
+    out = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    spk.spkadd_scan_counts_noalloc(counts, out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    spk.spkadd_scan_counts_noalloc(counts, out)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    assert int(out[-1].item()) == n
