@@ -55,6 +55,7 @@ WORKLOADS = {
     "er_k32_m2p20_n2p18_d16_f64": dict(family="er", k=32, m=1 << 20, n=1 << 18, d=16, dtype=torch.float64),
 }
 DEFAULT_WORKLOAD = "er_k32_m2p20_d16_f64"
+RMAT_WORKLOAD = "rmat_k64_s20_ef16_f32"
 
 
 def make_inputs(w, device, seed, n_override=None):
@@ -297,6 +298,80 @@ def run_reference(args, world, rank):
     }))
 
 
+def step_fn(spk, A, m, n, dtype, dev, stream, opts, method, ev=None, want_info=False):
+    """One step of the hot path on resident inputs: plan, (symbolic, B
+    allocation, numeric) or (B allocation, one pass), destroy.  `ev` brackets
+    the dominant kernel work (the numeric phase, or the one-pass launch)."""
+    h = spk.spkadd_plan(A, m, stream=stream, options=opts)
+    cp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    if method == "onepass":
+        cap = sum(a[1].numel() for a in A)
+        ri = torch.empty(cap, dtype=torch.int32, device=dev)
+        va = torch.empty(cap, dtype=dtype, device=dev)
+        if ev is not None:
+            ev[0].record(stream)
+        nnz = spk.spkadd_onepass(h, cp, ri, va)
+        if ev is not None:
+            ev[1].record(stream)
+    else:
+        nnz = spk.spkadd_symbolic(h)
+        ri = torch.empty(nnz, dtype=torch.int32, device=dev)
+        va = torch.empty(nnz, dtype=dtype, device=dev)
+        if ev is not None:
+            ev[0].record(stream)
+        spk.spkadd_numeric(h, cp, ri, va)
+        if ev is not None:
+            ev[1].record(stream)
+    info = spk.spkadd_get_info(h) if want_info else None  # (synchronises: never inside the timed region)
+    spk.spkadd_destroy(h)
+    return nnz, info
+
+
+def timed_steps(spk, A, m, n, dtype, dev, stream, opts, method, steps, warmup, world, rank, clocks=False):
+    """W untimed steps, then exactly K timed steps bracketed by a barrier and a
+    synchronize; returns (seconds per step (MAX over ranks), dominant-kernel ms
+    per step (CUDA events on the launching stream), nnz(B), info, clocks)."""
+    nnz, info = None, None
+    for i in range(max(warmup, 1)):
+        nnz, inf = step_fn(spk, A, m, n, dtype, dev, stream, opts, method, want_info=(i == 0))
+        info = inf or info
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sampler = ClockSampler(torch.cuda.current_device()) if clocks and rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(steps):
+        step_fn(spk, A, m, n, dtype, dev, stream, opts, method, events[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = sampler.stop() if sampler else None
+    barrier(world)
+    elapsed = reduce_max(t0.elapsed_time(t1) / 1e3, world)
+    kern_ms = reduce_max(sum(a.elapsed_time(b) for a, b in events) / steps, world)
+    return elapsed / steps, kern_ms, nnz, info, clk
+
+
+def cpu_baseline_of(A, cols, min_seconds=10.0):
+    S, stride = oracle_sample(A, cols)
+    nz_s, t_s, cores, reps = time_oracle(S, min_seconds=min_seconds)
+    return {"value": nz_s / t_s, "unit": "nnz/s", "cores": cores, "kind": "oracle",
+            "sample": f"every {stride}-th column of the workload ({len(S[0][0]) - 1} columns, {nz_s} input nnz), "
+                      f"{reps} runs of {t_s:.2f} s each"}
+
+
+def kernel_label(info, method):
+    if method == "onepass" and info.get("onepass"):
+        return "k_warp_onepass (spkadd_onepass)"
+    if info["cols_cta"] + info["cols_heavy"] == 0:
+        return "k_warp_col<numeric> (spkadd_numeric)"
+    return ("spkadd_numeric: k_warp_col<numeric> and the thread-block items' kernel "
+            "(k_num_compact or k_num_bitmap)")
+
+
 def run_ours(args, world, rank, local):
     import paper_2112_10223_gb300 as spk
 
@@ -313,60 +388,27 @@ def run_ours(args, world, rank, local):
                                    block_accumulator=args.block_accumulator)
     k = len(A)
     n = A[0][0].numel() - 1
-    vbytes = 8 if w["dtype"] == torch.float64 else 4
+    dtype = w["dtype"]
+    vbytes = 8 if dtype == torch.float64 else 4
     nnz_in = sum(a[1].numel() for a in A)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
 
-    def step(ev=None):
-        h = spk.spkadd_plan(A, m, stream=stream, options=opts)
-        nnz = spk.spkadd_symbolic(h)
-        cp = torch.empty(n + 1, dtype=torch.int64, device=dev)
-        ri = torch.empty(nnz, dtype=torch.int32, device=dev)
-        va = torch.empty(nnz, dtype=w["dtype"], device=dev)
-        if ev is not None:
-            ev[0].record(stream)
-        spk.spkadd_numeric(h, cp, ri, va)
-        if ev is not None:
-            ev[1].record(stream)
-        info = spk.spkadd_get_info(h) if args.info else None
-        spk.spkadd_destroy(h)
-        return nnz, info
-
-    nnz_out, info = None, None
-    for _ in range(max(args.warmup, 1)):
-        nnz_out, _ = step()
-    # launches per step, from one untimed step
-    h = spk.spkadd_plan(A, m, stream=stream, options=opts)
-    spk.spkadd_symbolic(h)
-    cp0 = torch.empty(n + 1, dtype=torch.int64, device=dev)
-    ri0 = torch.empty(nnz_out, dtype=torch.int32, device=dev)
-    va0 = torch.empty(nnz_out, dtype=w["dtype"], device=dev)
-    spk.spkadd_numeric(h, cp0, ri0, va0)
-    info = spk.spkadd_get_info(h)
-    spk.spkadd_destroy(h)
-    del cp0, ri0, va0
+    t_step, kern_ms, nnz_out, info, clk = timed_steps(spk, A, m, n, dtype, dev, stream, opts, args.method,
+                                                      args.steps, args.warmup, world, rank, clocks=True)
     launches_per_step = info["kernel_launches"]
+    peak, peak_src = read_peaks()
+    alg = algorithmic_bytes(k, n, nnz_in, nnz_out, vbytes)
 
-    num_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(args.steps)]
-    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    barrier(world)
-    torch.cuda.synchronize()
-    if clocks:
-        clocks.start()
-        time.sleep(0.3)
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for s in range(args.steps):
-        step(num_events[s])
-    t_end.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop() if clocks else None
-    barrier(world)
-    elapsed = reduce_max(t_start.elapsed_time(t_end) / 1e3, world)
-    num_ms = [a.elapsed_time(b) for a, b in num_events]
-    num_avg = reduce_max(sum(num_ms) / len(num_ms), world)
+    # The other method on the same inputs (context line: which path is faster here).
+    other = None
+    if args.compare_methods:
+        om = "onepass" if args.method == "twopass" else "twopass"
+        o_step, o_kern, _, o_info, _ = timed_steps(spk, A, m, n, dtype, dev, stream, opts, om, args.steps,
+                                                   args.warmup, world, rank)
+        other = {"method": om, "ms_per_step": o_step * 1e3, "value": world * nnz_in / o_step,
+                 "step_frac": alg / o_step / 1e9 / peak, "kernel_ms": o_kern, "kernel": kernel_label(o_info, om),
+                 "onepass_used": bool(o_info.get("onepass"))}
 
     cpu_sample, cpu_stride = (oracle_sample(A, args.oracle_cols) if rank == 0 and world == 1
                               and args.oracle_cols > 0 else (None, None))
@@ -381,7 +423,7 @@ def run_ours(args, world, rank, local):
         h2d = sum(t.numel() * t.element_size() for a in host for t in a)
         out_cp = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
         out_ri = torch.empty(nnz_out, dtype=torch.int32, pin_memory=True)
-        out_va = torch.empty(nnz_out, dtype=w["dtype"], pin_memory=True)
+        out_va = torch.empty(nnz_out, dtype=dtype, pin_memory=True)
         d2h = (n + 1) * 8 + nnz_out * (4 + vbytes)
         del A
         torch.cuda.empty_cache()
@@ -412,7 +454,7 @@ def run_ours(args, world, rank, local):
                     nz = spk.spkadd_symbolic(hh)
                     cp = torch.empty(n + 1, dtype=torch.int64, device=dev)
                     ri = torch.empty(nz, dtype=torch.int32, device=dev)
-                    va = torch.empty(nz, dtype=w["dtype"], device=dev)
+                    va = torch.empty(nz, dtype=dtype, device=dev)
                     spk.spkadd_numeric(hh, cp, ri, va)
                     out_cp.copy_(cp, non_blocking=True)
                     out_ri[:nz].copy_(ri, non_blocking=True)
@@ -429,44 +471,70 @@ def run_ours(args, world, rank, local):
         e2e = {"value": world * nnz_in * args.e2e_steps / te, "unit": "nnz/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "pipelining": "step i+1's H2D overlaps step i's compute and D2H (two streams, two input buffers)"}
-        del bufs
+        del bufs, host
     else:
         del A
+    torch.cuda.empty_cache()
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and args.oracle_cols > 0:
-        S = cpu_sample
-        nz_s, t_s, cores, reps = time_oracle(S, min_seconds=10.0)
+        nz_s, t_s, cores, reps = time_oracle(cpu_sample, min_seconds=10.0)
         cpu = {"value": nz_s / t_s, "unit": "nnz/s", "cores": cores, "kind": "oracle",
-               "sample": f"every {cpu_stride}-th column of the workload ({len(S[0][0]) - 1} columns, "
+               "sample": f"every {cpu_stride}-th column of the workload ({len(cpu_sample[0][0]) - 1} columns, "
                          f"{nz_s} input nnz), {reps} runs of {t_s:.2f} s each"}
+
+    # The skewed R-MAT workload (k = 64, scale 20, fp32) in the same run, as a
+    # second line under its own key: the default invocation measures both
+    # single-instance workloads that the roofline target names.
+    extra = {}
+    if args.extra_rmat and args.workload == DEFAULT_WORKLOAD:
+        wr = WORKLOADS[RMAT_WORKLOAD]
+        R, mr = make_inputs(wr, dev, seed=args.seed + rank)
+        kr, nr = len(R), R[0][0].numel() - 1
+        nnz_r = sum(a[1].numel() for a in R)
+        r_step, r_kern, r_nnz, r_info, r_clk = timed_steps(spk, R, mr, nr, wr["dtype"], dev, stream, None, "twopass",
+                                                           args.steps, args.warmup, world, rank, clocks=True)
+        alg_r = algorithmic_bytes(kr, nr, nnz_r, r_nnz, 4)
+        extra[RMAT_WORKLOAD] = {
+            "value": world * nnz_r / r_step, "unit": "nnz/s", "ms_per_step": r_step * 1e3, "steps": args.steps,
+            "warmup": args.warmup, "dtype": "f32",
+            "config": {"workload": RMAT_WORKLOAD, "k": kr, "m": mr, "n": nr, "nnz_in": nnz_r, "nnz_out": r_nnz,
+                       "cf": nnz_r / max(r_nnz, 1)},
+            "hbm_gbs_step": alg_r / r_step / 1e9,
+            "roofline": {"kernel": kernel_label(r_info, "twopass"), "bound": "hbm",
+                         "achieved": alg_r / (r_kern / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg_r / (r_kern / 1e3) / 1e9 / peak, "peak_source": peak_src, "traffic": None,
+                         "algorithmic_bytes": alg_r, "launch_ms": r_kern, "step_frac": alg_r / r_step / 1e9 / peak},
+            "cpu_baseline": (cpu_baseline_of(R, args.oracle_cols // 4) if rank == 0 and world == 1
+                             and args.oracle_cols > 0 else None),
+            "clocks": r_clk, "gpu_launches": r_info["kernel_launches"] * args.steps,
+            "classes": {x: r_info[x] for x in ("cols_warp", "cols_cta", "cols_heavy", "windows", "windows_split")},
+        }
+        del R
+        torch.cuda.empty_cache()
 
     if rank != 0:
         return
-    peak, peak_src = read_peaks()
-    alg = algorithmic_bytes(k, n, nnz_in, nnz_out, vbytes)
-    achieved = alg / (num_avg / 1e3) / 1e9
-    step_gbs = alg / (elapsed / args.steps) / 1e9
+    achieved = alg / (kern_ms / 1e3) / 1e9
+    step_gbs = alg / t_step / 1e9
     out = {
-        "metric": METRIC, "value": world * nnz_in * args.steps / elapsed, "unit": "nnz/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+        "metric": METRIC, "value": world * nnz_in / t_step, "unit": "nnz/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if vbytes == 8 else "f32", "data": "synthetic",
         "config": {"workload": args.workload, "k": k, "m": m, "n": n, "nnz_in": nnz_in, "nnz_out": nnz_out,
                    "cf": nnz_in / max(nnz_out, 1), "l2": "inputs exceed the 129 MB L2; no flush between steps",
                    "parallelism": f"{world} independent instance(s), one per GPU", "seed": args.seed,
+                   "method": args.method,
                    "input_order": "rows shuffled inside columns" if args.unordered else "sorted",
                    "output_order": "any order inside a column" if args.unsorted_output else "sorted",
                    "block_accumulator": ("automatic", "flat bitmap", "compact word table")[args.block_accumulator]},
         "hbm_gbs_step": step_gbs,
-        "roofline": {"kernel": ("k_warp_col<numeric> (spkadd_numeric)" if info["cols_cta"] + info["cols_heavy"] == 0
-                                else "spkadd_numeric: k_warp_col<numeric> and the thread-block items' kernel "
-                                     "(k_num_compact or k_num_bitmap)"),
-                     "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": kernel_label(info, args.method), "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": read_traffic(args.workload), "algorithmic_bytes": alg,
-                     "launch_ms": num_avg, "step_frac": step_gbs / peak},
+                     "launch_ms": kern_ms, "step_frac": step_gbs / peak},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
@@ -474,6 +542,9 @@ def run_ours(args, world, rank, local):
         "classes": {x: info[x] for x in ("cols_warp", "cols_cta", "cols_heavy", "windows", "windows_split",
                                          "cols_unique")},
     }
+    if other:
+        out["other_method"] = other
+    out.update(extra)
     print(json.dumps(out))
 
 
@@ -971,6 +1042,12 @@ def main():
     ap.add_argument("--oracle-cols", type=int, default=1 << 20,
                     help="columns of the CPU oracle's sample (every (n / cols)-th column)")
     ap.add_argument("--info", action="store_true")
+    ap.add_argument("--method", choices=["twopass", "onepass"], default="twopass",
+                    help="twopass: spkadd_symbolic + spkadd_numeric; onepass: spkadd_onepass")
+    ap.add_argument("--no-compare-methods", dest="compare_methods", action="store_false",
+                    help="skip timing the other method on the same inputs")
+    ap.add_argument("--no-extra-rmat", dest="extra_rmat", action="store_false",
+                    help="skip the R-MAT line that the default workload's run adds")
     ap.add_argument("--unordered", action="store_true",
                     help="shuffle rows inside every input column and run with input_order = 1")
     ap.add_argument("--unsorted-output", action="store_true", help="run with sort_mode = 2 (B's columns unsorted)")
