@@ -299,7 +299,7 @@ static spkadd_status plan_problems(spkadd_handle** hp, bool batch, int count, co
   const size_t o_u = cv.take<int32_t>(ncols);
   const size_t o_wl = cv.take<int32_t>(ncols);
   const size_t o_cl = cv.take<int32_t>(ncols);
-  const size_t o_hl = cv.take<int32_t>(ncols);
+  const size_t o_hl = cv.take<int32_t>(2 * ncols);
   const size_t o_win = cv.take<Window>(win_cap);
   const size_t o_srch = cv.take<int32_t>(win_cap);
   const size_t o_colp = cv.take<int64_t>(ncols + 1);
@@ -553,7 +553,7 @@ SPK_API spkadd_status spkadd_onepass(spkadd_handle* h, int64_t* B_col_ptr, int32
   spkadd_status ds = from_device_err(pb->ctr.err);
   if (ds != SPKADD_OK) return ds;
   const Counters c = pb->ctr;
-  const bool fits = h->ncols > 0 && c.n_cta == 0 && c.n_heavy == 0 && h->dt_mode != 2;
+  const bool fits = h->ncols > 0 && c.n_cta == 0 && c.n_heavy == 0 && c.n_big == 0 && h->dt_mode != 2;
   if (!fits) {
     h->onepass = false;
     spkadd_status s = SPKADD_OK;
@@ -640,7 +640,7 @@ SPK_API spkadd_status spkadd_get_info(spkadd_handle* h, spkadd_info* info) {
   const Counters c = pb->ctr;
   info->cols_warp = c.n_warp;
   info->cols_cta = c.n_cta;
-  info->cols_heavy = c.n_heavy;
+  info->cols_heavy = (int64_t)c.n_heavy + c.n_big;
   info->windows = c.n_windows;
   info->windows_split = c.n_search;
   info->cols_unique = c.n_unique;

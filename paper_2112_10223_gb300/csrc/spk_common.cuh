@@ -39,8 +39,14 @@ struct Counters {
   int32_t n_search;     // of those, split windows needing per-input offsets
   int32_t n_unique;     // warp columns whose input rows are all distinct (u_j == s_j)
   int32_t err;
-  int32_t pad;
+  int32_t n_big;        // heavy columns with s_j > BIG_S (listed apart, counted in n_heavy too)
+  int32_t heavy_next;   // work counter of the heavy-column symbolic kernels
+  int32_t pad[3];
 };
+
+// Heavy columns above this summed input count are listed apart and handed out
+// first (largest work first keeps one huge R-MAT column from finishing last).
+constexpr int32_t BIG_S = 1 << 18;
 
 // One SpKAdd problem of a batch, as the kernels see it.  A single call is a
 // batch of one.  Columns of all problems are numbered in one global column

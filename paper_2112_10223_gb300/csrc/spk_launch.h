@@ -29,6 +29,8 @@ struct DeviceInfo {
 // 0 on error.
 int resident_blocks(const void* fn, int block, size_t smem);
 
+// heavy_list holds 2 * ncols entries: heavy columns with s_j <= BIG_S from the
+// start, the larger ones from entry ncols (Counters::n_heavy, ::n_big).
 cudaError_t launch_bin(const Inputs& in, int warp_max, int cta_max, int32_t* s, int32_t* u, int32_t* warp_list,
                        int32_t* cta_list, int32_t* heavy_list, Counters* ctr, int sms, cudaStream_t st);
 // Batch: col_inst[colbase + j] = q for every column j of every problem q.

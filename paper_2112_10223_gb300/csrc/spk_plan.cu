@@ -24,6 +24,7 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t* __restrict__ lis
 __global__ void __launch_bounds__(256) k_bin(Inputs in, int warp_max, int cta_max, int32_t* __restrict__ s_out,
                                              int32_t* __restrict__ u_out, int32_t* __restrict__ warp_list,
                                              int32_t* __restrict__ cta_list, int32_t* __restrict__ heavy_list,
+                                             int32_t* __restrict__ big_list,
                                              Counters* __restrict__ ctr) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -55,7 +56,9 @@ __global__ void __launch_bounds__(256) k_bin(Inputs in, int warp_max, int cta_ma
     }
     warp_append(cls == CLS_WARP, warp_list, &ctr->n_warp, g, lane);
     warp_append(cls == CLS_CTA, cta_list, &ctr->n_cta, g, lane);
-    warp_append(cls == CLS_HEAVY, heavy_list, &ctr->n_heavy, g, lane);
+    // Heavy columns: the largest go to their own list, handed out first.
+    warp_append(cls == CLS_HEAVY && s <= BIG_S, heavy_list, &ctr->n_heavy, g, lane);
+    warp_append(cls == CLS_HEAVY && s > BIG_S, big_list, &ctr->n_big, g, lane);
   }
 }
 
@@ -251,7 +254,7 @@ cudaError_t launch_bin(const Inputs& in, int warp_max, int cta_max, int32_t* s, 
   if (in.ncols == 0) return cudaSuccess;
   int64_t blocks = ((int64_t)in.ncols + 255) / 256;
   if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
-  k_bin<<<(int)blocks, 256, 0, st>>>(in, warp_max, cta_max, s, u, wl, cl, hl, ctr);
+  k_bin<<<(int)blocks, 256, 0, st>>>(in, warp_max, cta_max, s, u, wl, cl, hl, hl + in.ncols, ctr);
   return cudaGetLastError();
 }
 

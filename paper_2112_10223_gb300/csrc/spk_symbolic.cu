@@ -108,7 +108,8 @@ constexpr int MAX_SLAB_WINDOWS = 1100;  // 2^20 rows / (1024 - 64) + 2
 constexpr int FILTER_WINDOWS = 3;       // see the window records below
 constexpr int FILTER_SEG = 64;
 
-// Heavy columns: one thread block per column.  Rows of one slab of 2^20 rows
+// Heavy columns: one thread block per column (from a work counter, columns
+// with s_j > BIG_S first).  Rows of one slab of 2^20 rows
 // at a time go into a 64-bit-word bitmap plus a summary bitmap (one bit per
 // non-empty word), both kept zero between slabs, so the work per slab grows
 // with the rows present, not with the slab.  The popcount prefix over the
@@ -135,10 +136,18 @@ __global__ void __launch_bounds__(BLOCK, BLOCK >= 1024 ? 1 : 4) k_sym_heavy(Inpu
   for (int x = threadIdx.x; x < W64; x += BLOCK) bm[x] = 0ull;
   for (int x = threadIdx.x; x < NSW; x += BLOCK) summ[x] = 0u;
   __syncthreads();
-  const int ncols = ctr->n_heavy;
+  const int n_big = ctr->n_big;
+  const int ncols = n_big + ctr->n_heavy;
   const int slab_rows = 1 << slab_log2;
-  for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
-    const int g = list[c];
+  __shared__ int s_next;
+  // Columns are handed out by a work counter, the largest list first.
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(&ctr_w->heavy_next, 1);
+    __syncthreads();
+    const int c = s_next;
+    __syncthreads();
+    if (c >= ncols) break;
+    const int g = c < n_big ? list[in.ncols + c] : list[c - n_big];
     const Inst* I = in.inst + inst_of(in, g);
     const int k = I->k, off = I->ptr_off, m = I->m, j = g - I->colbase;
     const int nslabs = (int)(((int64_t)m + slab_rows - 1) / slab_rows);
@@ -320,11 +329,19 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy_compact(Inputs in, const in
   for (int x = threadIdx.x; x < NSW; x += BLOCK) summ[x] = 0u;
   for (int x = threadIdx.x; x < cap; x += BLOCK) cw[x] = 0u;
   __syncthreads();
-  const int ncols = ctr->n_heavy;
+  const int n_big = ctr->n_big;
+  const int ncols = n_big + ctr->n_heavy;
   const int slab_rows = 1 << slab_log2;
   const int capw = cap - 32;  // a sub-range starts below capw words: it ends below cap
-  for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
-    const int g = list[c];
+  __shared__ int s_next;
+  // Columns are handed out by a work counter, the largest list first.
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(&ctr_w->heavy_next, 1);
+    __syncthreads();
+    const int c = s_next;
+    __syncthreads();
+    if (c >= ncols) break;
+    const int g = c < n_big ? list[in.ncols + c] : list[c - n_big];
     const Inst* I = in.inst + inst_of(in, g);
     const int k = I->k, off = I->ptr_off, m = I->m, j = g - I->colbase;
     const int nslabs = (int)(((int64_t)m + slab_rows - 1) / slab_rows);
