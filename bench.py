@@ -363,6 +363,48 @@ def cpu_baseline_of(A, cols, min_seconds=10.0):
                       f"{reps} runs of {t_s:.2f} s each"}
 
 
+def pairwise_tree(A, m):
+    """The 2-way tree of Sec. II-B (the paper's "2-way Tree" / "MKL Tree"
+    comparison systems) on this GPU: inputs added in pairs, level by level,
+    each addition done by cuSPARSE (csrgeam2, reached through torch.add on
+    sparse CSR tensors: a CSC matrix is the CSR form of its transpose).
+    Returns (col_ptr, row_idx, val) of the sum."""
+    import warnings
+
+    warnings.filterwarnings("ignore", message="Sparse CSR tensor support is in beta state")
+    n = A[0][0].numel() - 1
+    level = [torch.sparse_csr_tensor(cp, ri, va, size=(n, m), check_invariants=False) for cp, ri, va in A]
+    while len(level) > 1:
+        nxt = [torch.add(level[i], level[i + 1]) for i in range(0, len(level) - 1, 2)]
+        if len(level) % 2:
+            nxt.append(level[-1])
+        level = nxt
+    B = level[0]
+    return B.crow_indices(), B.col_indices(), B.values()
+
+
+def time_pairwise_tree(A, m, ours, steps, warmup):
+    """Per-step time of pairwise_tree on resident inputs (CUDA events), and
+    whether its result equals ours (indices exactly, values within the parity
+    tolerance)."""
+    for _ in range(max(warmup, 1)):
+        B = pairwise_tree(A, m)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        B = pairwise_tree(A, m)
+    e1.record()
+    torch.cuda.synchronize()
+    cp, ri, va = ours
+    same_idx = (B[0].numel() == cp.numel() and bool(torch.equal(B[0].to(torch.int64), cp))
+                and bool(torch.equal(B[1].to(torch.int32), ri)))
+    tol = 1e-12 if va.dtype == torch.float64 else 1e-5
+    same_val = same_idx and bool(((B[2].to(torch.float64) - va.to(torch.float64)).abs()
+                                  <= tol * len(A) * (va.to(torch.float64).abs() + 1)).all())
+    return e0.elapsed_time(e1) / steps, same_idx, same_val
+
+
 def kernel_label(info, method):
     if method == "onepass" and info.get("onepass"):
         return "k_warp_onepass (spkadd_onepass)"
@@ -409,6 +451,19 @@ def run_ours(args, world, rank, local):
         other = {"method": om, "ms_per_step": o_step * 1e3, "value": world * nnz_in / o_step,
                  "step_frac": alg / o_step / 1e9 / peak, "kernel_ms": o_kern, "kernel": kernel_label(o_info, om),
                  "onepass_used": bool(o_info.get("onepass"))}
+
+    # Context for Sec. II-C's claim that k-way beats 2-way: the same sum as a
+    # pairwise tree of cuSPARSE additions on this GPU.
+    tree = None
+    if args.pairwise_tree and args.workload == DEFAULT_WORKLOAD and not args.unordered:
+        ours = spk.spkadd(A, m, method=args.method)
+        t_ms, same_idx, same_val = time_pairwise_tree(A, m, ours, max(2, args.steps // 3), 2)
+        del ours
+        torch.cuda.empty_cache()
+        tree = {"system": "pairwise tree of cuSPARSE csrgeam2 additions (torch.add on sparse CSR), "
+                          f"{k - 1} additions in {math.ceil(math.log2(max(k, 2)))} levels",
+                "ms_per_step": t_ms, "value": world * nnz_in / (t_ms / 1e3), "unit": "nnz/s",
+                "kway_speedup": t_ms / (t_step * 1e3), "same_indices": same_idx, "same_values": same_val}
 
     cpu_sample, cpu_stride = (oracle_sample(A, args.oracle_cols) if rank == 0 and world == 1
                               and args.oracle_cols > 0 else (None, None))
@@ -544,6 +599,8 @@ def run_ours(args, world, rank, local):
     }
     if other:
         out["other_method"] = other
+    if tree:
+        out["pairwise_tree"] = tree
     out.update(extra)
     print(json.dumps(out))
 
@@ -733,12 +790,12 @@ def run_batch(args, world, rank, local):
         if rank == 0 and args.batch_verify > 0:
             import oracle
 
-            small = sorted(range(len(wave)), key=lambda i: nnz_in[i])
-            picks = small[:1] + [small[len(small) // 2]][: args.batch_verify - 1]
+            # a size-stratified sample: instances evenly spaced in the wave's size order
+            by_size = sorted(range(len(wave)), key=lambda i: nnz_in[i])
+            nv = min(args.batch_verify, len(by_size))
+            picks = sorted({by_size[round(q * (len(by_size) - 1) / max(nv - 1, 1))] for q in range(nv)})
             cp_all, ri_all, v64, v32 = res[0], res[1], res[2], res[3]
             for i in picks:
-                if nnz_in[i] > 6e7:
-                    continue
                 A, m = probs[i]
                 An = [tuple(t.cpu().numpy() for t in a) for a in A]
                 t0 = time.perf_counter()
@@ -1046,6 +1103,8 @@ def main():
                     help="twopass: spkadd_symbolic + spkadd_numeric; onepass: spkadd_onepass")
     ap.add_argument("--no-compare-methods", dest="compare_methods", action="store_false",
                     help="skip timing the other method on the same inputs")
+    ap.add_argument("--no-pairwise-tree", dest="pairwise_tree", action="store_false",
+                    help="skip timing the cuSPARSE pairwise-tree sum beside the k-way path")
     ap.add_argument("--no-extra-rmat", dest="extra_rmat", action="store_false",
                     help="skip the R-MAT line that the default workload's run adds")
     ap.add_argument("--unordered", action="store_true",
@@ -1055,7 +1114,8 @@ def main():
                     help="thread-block items' accumulator: 0 automatic, 1 flat bitmap, 2 compact word table")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--batch-mem-frac", type=float, default=0.55, help="device memory share of one wave")
-    ap.add_argument("--batch-verify", type=int, default=2, help="instances per wave checked against the oracle")
+    ap.add_argument("--batch-verify", type=int, default=32,
+                    help="instances per wave checked against the oracle (evenly spaced in size order)")
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests per served trace")
     ap.add_argument("--serve-pool-frac", type=float, default=0.3, help="device memory share of the input pool")
     ap.add_argument("--serve-pool-max", type=int, default=512, help="most distinct requests in the input pool")

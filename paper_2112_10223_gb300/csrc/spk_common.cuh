@@ -44,6 +44,13 @@ struct Counters {
   int32_t pad[3];
 };
 
+// Float inputs are accumulated in float while no output entry can collect more
+// terms than this (k <= 167): recursive summation errs by at most
+// (t - 1) 2^-24 sum|terms| plus one final rounding, within 1e-5 sum|terms|.
+// Beyond it the thread-block accumulators use double; warp columns always sum
+// a row's run in double.
+constexpr int FP32_ACC_TERMS = 167;
+
 // Heavy columns above this summed input count are listed apart and handed out
 // first (largest work first keeps one huge R-MAT column from finishing last).
 constexpr int32_t BIG_S = 1 << 18;

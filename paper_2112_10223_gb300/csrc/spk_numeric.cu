@@ -99,13 +99,13 @@ __device__ __forceinline__ uint32_t own_word_mask(const uint32_t* summ, int w0, 
 
 // One item (a CTA-class column or a heavy column's row window [r_lo, r_hi),
 // Alg. 8: B(r1:r2, j) <- HashAdd(A_1(r1:r2, j), ..., A_k(r1:r2, j))).
-template <typename V, int BLOCK, int U>
+template <typename V, typename A, int BLOCK, int U>
 __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, const Inst* I, const int32_t* offs,
                                             int32_t* __restrict__ out_row, V* __restrict__ out_val,
                                             const BitmapSmem& sm, int slab_log2, Counters* ctr_w) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int k = I->k, off = I->ptr_off, j = W.col - I->colbase;
-  V* acc = reinterpret_cast<V*>(sm.acc);
+  A* acc = reinterpret_cast<A*>(sm.acc);
   const int64_t S = (int64_t)1 << slab_log2;
   const int64_t span = (int64_t)W.r_hi - W.r_lo;
   const int nsl = span <= 0 ? 0 : (int)((span + S - 1) >> slab_log2);
@@ -175,7 +175,7 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
         sm.nel[pos++] = (uint16_t)w;
         rank += __popcll(sm.bm[w]);
       }
-      for (int q = threadIdx.x; q < slab_u; q += BLOCK) acc[q] = V(0);
+      for (int q = threadIdx.x; q < slab_u; q += BLOCK) acc[q] = A(0);
     } else {
       bad = true;
     }
@@ -189,7 +189,7 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
           const unsigned long long bits = sm.bm[w];
           const uint32_t below = rr & 63;
           const int q = (int)sm.wpre[w] + __popcll(below ? (bits << (64 - below)) : 0ull);
-          if (bits && q < slab_u) atomicAdd(&acc[q], v);
+          if (bits && q < slab_u) atomicAdd(&acc[q], (A)v);
         }
         return 0u;
       };
@@ -211,7 +211,7 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
       V* oval = out_val + u_done;
       for (int q = threadIdx.x; q < lim; q += BLOCK) {
         orow[q] = sm.rows[q];
-        oval[q] = acc[q];
+        oval[q] = (V)acc[q];
       }
       u_done += slab_u;
     }
@@ -259,12 +259,12 @@ __device__ __forceinline__ int compact_index(const CompactSmem& sm, uint32_t w) 
   return (int)sm.spre[x] + __popc(sm.summ[x] & ((1u << (w & 31)) - 1u));
 }
 
-template <typename V, int BLOCK, int U>
+template <typename V, typename A, int BLOCK, int U>
 __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, const Inst* I, const int32_t* offs,
                                              int32_t* __restrict__ out_row, V* __restrict__ out_val,
                                              const CompactSmem& sm, int slab_log2, Counters* ctr_w) {
   const int k = I->k, off = I->ptr_off, j = W.col - I->colbase;
-  V* acc = reinterpret_cast<V*>(sm.acc);
+  A* acc = reinterpret_cast<A*>(sm.acc);
   const int64_t S = (int64_t)1 << slab_log2;
   const int64_t span = (int64_t)W.r_hi - W.r_lo;
   const int nsl = span <= 0 ? 0 : (int)((span + S - 1) >> slab_log2);
@@ -352,7 +352,7 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
           sm.wpre[cc] = (uint16_t)rank;
           rank += __popc(sm.cw[cc]);
         }
-        for (int q = threadIdx.x; q < slab_u; q += BLOCK) acc[q] = V(0);
+        for (int q = threadIdx.x; q < slab_u; q += BLOCK) acc[q] = A(0);
       } else {
         bad = true;
       }
@@ -367,7 +367,7 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
           if (cc < ne) {
             const uint32_t bits = sm.cw[cc], b = rr & 31;
             const int q = (int)sm.wpre[cc] + __popc(bits & ((1u << b) - 1u));
-            if (((bits >> b) & 1u) && q < slab_u) atomicAdd(&acc[q], v);
+            if (((bits >> b) & 1u) && q < slab_u) atomicAdd(&acc[q], (A)v);
           }
         }
         return 0u;
@@ -388,7 +388,7 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
           ++q;
         }
       }
-      for (int q = threadIdx.x; q < lim; q += BLOCK) oval[q] = acc[q];
+      for (int q = threadIdx.x; q < lim; q += BLOCK) oval[q] = (V)acc[q];
       u_done += slab_u;
       __syncthreads();
     }
@@ -401,19 +401,20 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
   if (threadIdx.x == 0 && (bad || u_done != W.u)) atomicOr(&ctr_w->err, ERR_INTERNAL);
 }
 
-template <int DT, int BLOCK, int U>
+template <int DT, bool WIDE, int BLOCK, int U>
 __global__ void __launch_bounds__(BLOCK) k_num_compact(Inputs in, const Window* __restrict__ win, int nwin,
                                                        const int32_t* __restrict__ offs,
                                                        const int64_t* __restrict__ col_ptr, Outs o, int slab_log2,
                                                        int umax, int only_dtype, Counters* ctr_w) {
   using V = typename std::conditional<DT == 1, double, float>::type;
+  using A = typename std::conditional<DT == 1 || WIDE, double, float>::type;  // accumulator
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int red[BLOCK / 32 + 1];
   CompactSmem sm;
   sm.NSW = 1 << (slab_log2 - 10);
   sm.umax = umax;
   sm.acc = sm_raw;
-  sm.summ = reinterpret_cast<uint32_t*>(sm.acc + (size_t)umax * sizeof(V));
+  sm.summ = reinterpret_cast<uint32_t*>(sm.acc + (size_t)umax * sizeof(A));
   sm.cw = sm.summ + sm.NSW;
   sm.spre = reinterpret_cast<uint16_t*>(sm.cw + umax);
   sm.wpre = sm.spre + sm.NSW;
@@ -431,19 +432,20 @@ __global__ void __launch_bounds__(BLOCK) k_num_compact(Inputs in, const Window* 
     const Inst* I = in.inst + q;
     if (only_dtype >= 0 && I->dtype != only_dtype) continue;
     const int64_t out = col_ptr[W.col] - (in.col_inst ? col_ptr[I->colbase] : 0) + W.out_off;
-    compact_item<V, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
+    compact_item<V, A, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
                               slab_log2, ctr_w);
   }
 }
 
 // DT: 0 = float values, 1 = double values.  A batch mixing both runs the
 // kernel once per dtype; only_dtype >= 0 then skips the other dtype's items.
-template <int DT, int BLOCK, int U>
+template <int DT, bool WIDE, int BLOCK, int U>
 __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* __restrict__ win, int nwin,
                                                       const int32_t* __restrict__ offs,
                                                       const int64_t* __restrict__ col_ptr, Outs o, int slab_log2,
                                                       int umax, int only_dtype, Counters* ctr_w) {
   using V = typename std::conditional<DT == 1, double, float>::type;
+  using A = typename std::conditional<DT == 1 || WIDE, double, float>::type;  // accumulator
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ unsigned long long red[BLOCK / 32 + 1];
   BitmapSmem sm;
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
   sm.umax = umax;
   sm.bm = reinterpret_cast<unsigned long long*>(sm_raw);
   sm.acc = reinterpret_cast<unsigned char*>(sm.bm + sm.W64);
-  sm.wpre = reinterpret_cast<uint16_t*>(sm.acc + (size_t)umax * sizeof(V));
+  sm.wpre = reinterpret_cast<uint16_t*>(sm.acc + (size_t)umax * sizeof(A));
   sm.summ = reinterpret_cast<uint32_t*>(sm.wpre + ((sm.W64 + 1) & ~1));
   sm.rows = reinterpret_cast<int32_t*>(sm.summ + sm.NSW);
   sm.nel = reinterpret_cast<uint16_t*>(sm.rows + umax);
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
     const Inst* I = in.inst + q;
     if (only_dtype >= 0 && I->dtype != only_dtype) continue;
     const int64_t out = col_ptr[W.col] - (in.col_inst ? col_ptr[I->colbase] : 0) + W.out_off;
-    bitmap_item<V, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
+    bitmap_item<V, A, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
                              slab_log2, ctr_w);
   }
 }
@@ -537,11 +539,11 @@ static cudaError_t launch_items(K kern, int block, int blocks_per_sm, const Inpu
 // Automatic takes the compact table when more of its blocks are resident per
 // SM (the flat bitmap's size follows the slab, the table's follows umax):
 // items are latency chains, so items in flight per SM decide the rate.
-template <int DT>
+template <int DT, bool WIDE>
 static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_win, const int32_t* offs,
                                     const int64_t* col_ptr, const Outs& out, int umax, int accumulator,
                                     int only_dtype, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
-  constexpr size_t VS = DT == 1 ? 8 : 4;
+  constexpr size_t VS = (DT == 1 || WIDE) ? 8 : 4;  // accumulator bytes
   int slab_log2 = 10;
   while (slab_log2 < NUM_SLAB_LOG2_MAX && ((int64_t)1 << slab_log2) < (int64_t)in.mmax) ++slab_log2;
   const size_t sf = bitmap_smem_bytes(slab_log2, umax, VS), sc = compact_smem_bytes(slab_log2, umax, VS);
@@ -549,19 +551,19 @@ static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_w
   // (measured best, with 8 entries per lane and round); a bitmap that fills
   // the SM gets one 1024-thread block.
   const bool small = sf <= (size_t)dev.smem_per_sm / 2 - 2048;
-  const void* kf = small ? (const void*)k_num_bitmap<DT, 256, 8> : (const void*)k_num_bitmap<DT, 1024, 4>;
-  const void* kc = (const void*)k_num_compact<DT, 256, 8>;
+  const void* kf = small ? (const void*)k_num_bitmap<DT, WIDE, 256, 8> : (const void*)k_num_bitmap<DT, WIDE, 1024, 4>;
+  const void* kc = (const void*)k_num_compact<DT, WIDE, 256, 8>;
   int bf = 0, bc = 0;
   if (accumulator != 2 && sf <= (size_t)dev.smem_optin) bf = resident_blocks(kf, small ? 256 : 1024, sf);
   if (accumulator != 1 && sc <= (size_t)dev.smem_optin) bc = resident_blocks(kc, 256, sc);
   const bool compact = accumulator == 2 || (accumulator == 0 && bc > bf);
   if (compact)
-    return launch_items(k_num_compact<DT, 256, 8>, 256, bc, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sc,
+    return launch_items(k_num_compact<DT, WIDE, 256, 8>, 256, bc, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sc,
                         only_dtype, ctr_w, dev, st);
   if (small)
-    return launch_items(k_num_bitmap<DT, 256, 8>, 256, bf, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sf,
+    return launch_items(k_num_bitmap<DT, WIDE, 256, 8>, 256, bf, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sf,
                         only_dtype, ctr_w, dev, st);
-  return launch_items(k_num_bitmap<DT, 1024, 4>, 1024, bf, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sf,
+  return launch_items(k_num_bitmap<DT, WIDE, 1024, 4>, 1024, bf, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sf,
                       only_dtype, ctr_w, dev, st);
 }
 
@@ -569,14 +571,23 @@ cudaError_t launch_num_cta(const Inputs& in, int dt, const Window* win, int n_wi
                            const int64_t* col_ptr, const Outs& out, int window_max, int accumulator, Counters* ctr_w,
                            const DeviceInfo& dev, cudaStream_t st) {
   if (n_win <= 0) return cudaSuccess;
-  if (dt == 0)
-    return launch_num_cta_t<0>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st);
+  // Float values are summed in float while no output entry can have more
+  // than FP32_ACC_TERMS terms (k <= 167: the error bound of the fp32
+  // tolerance holds), else in double.
+  const bool wide = in.kmax > FP32_ACC_TERMS;
+  auto launch_f32 = [&](int only) {
+    return wide ? launch_num_cta_t<0, true>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, only, ctr_w,
+                                            dev, st)
+                : launch_num_cta_t<0, false>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, only, ctr_w,
+                                             dev, st);
+  };
+  if (dt == 0) return launch_f32(-1);
   if (dt == 1)
-    return launch_num_cta_t<1>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st);
+    return launch_num_cta_t<1, false>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st);
   // Mixed batch: one launch per dtype, each skipping the other dtype's items.
-  cudaError_t e = launch_num_cta_t<0>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, 0, ctr_w, dev, st);
+  cudaError_t e = launch_f32(0);
   if (e == cudaSuccess)
-    e = launch_num_cta_t<1>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, 1, ctr_w, dev, st);
+    e = launch_num_cta_t<1, false>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, 1, ctr_w, dev, st);
   return e;
 }
 

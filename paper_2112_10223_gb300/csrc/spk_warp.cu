@@ -467,12 +467,12 @@ __device__ __forceinline__ void write_sorted(const int32_t* skey, const V* sval,
     const bool lead = q < s && key != prev;
     const unsigned bal = __ballot_sync(SPK_FULL, lead);
     if (lead) {
-      V sum = sval[q];
-      for (int y = q + 1; y < s && skey[y] == key; ++y) sum += sval[y];
+      double sum = (double)sval[q];  // float runs round once, at the end
+      for (int y = q + 1; y < s && skey[y] == key; ++y) sum += (double)sval[y];
       const int pos = before + __popc(bal & ((1u << lane) - 1u));
       if (pos < u) {
         out_row[pos] = key;
-        out_val[pos] = sum;
+        out_val[pos] = (V)sum;
       }
     }
     before += __popc(bal);

@@ -653,3 +653,28 @@ def test_accumulators_heavy_column_many_subranges(acc, order):
     opt = spk.default_options(window_max=1024, block_accumulator=acc, input_order=1 if order == "unordered" else 0)
     info, _ = check_full(A, m, F64, exact=True, options=opt)
     assert info["cols_heavy"] == 2 and info["windows"] > 60, info
+
+
+# ---------------------------------------------------------------------------
+# fp32 with many terms per output entry: past 167 inputs the thread-block
+# accumulators sum in double, and warp columns always sum a row's run in
+# double, so the 1e-5 * sum|terms| bar holds for any k.
+# ---------------------------------------------------------------------------
+def test_fp32_k300_every_class_within_bound():
+    """k = 300 SpGEMM-like fp32 inputs (each row in about a quarter of the inputs): warp, CTA and heavy items."""
+    A = synth.spgemm_like(300, 512, 120, 4, seed=12, dtype=F32)
+    opt = spk.default_options(warp_max=256, cta_max=1024, window_max=1024)
+    for method in ("twopass", "onepass"):
+        cp, ri, va, info = run_gpu(A, 512, options=opt, info=True, method=method)
+        compare((cp.cpu().numpy(), ri.cpu().numpy(), va.cpu().numpy()), oracle.add(to_np(A)), F32)
+    assert info["cols_cta"] + info["cols_heavy"] > 0
+
+
+def test_fp32_many_terms_per_entry():
+    """k = 1024 SpGEMM-like fp32 inputs of 8 rows per column drawn from 32 candidates: an output entry collects
+    about 256 terms (well past 167, and past the k <= 512 of the served workload)."""
+    A = synth.spgemm_like(1024, 1 << 12, 16, 8, seed=13, dtype=F32)
+    want = oracle.add(to_np(A))
+    assert want["terms"].max() > 167
+    cp, ri, va = run_gpu(A, 1 << 12)
+    compare((cp.cpu().numpy(), ri.cpu().numpy(), va.cpu().numpy()), want, F32)
