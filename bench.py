@@ -726,22 +726,18 @@ def run_batch(args, world, rank, local):
         torch.cuda.synchronize()
         desc = _descriptors(probs)
         nnz_in = np.asarray([len(A) * A[0][1].numel() for A, _ in probs], dtype=np.int64)
-        if tuned is None:  # pick the class thresholds on the first wave
-            cands = [dict(warp_max=512, cta_max=4096), dict(warp_max=256, cta_max=4096),
-                     dict(warp_max=512, cta_max=2048), dict(warp_max=128, cta_max=1024)]
-            best = None
-            for c in cands:
-                o = spk.default_options(**c)
-                batch_once(spk, desc, dev, stream, o)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                batch_once(spk, desc, dev, stream, o)
-                torch.cuda.synchronize()
-                t = time.perf_counter() - t0
-                tune_log.append(dict(c, ms=t * 1e3))
-                if best is None or t < best[0]:
-                    best = (t, c)
-            tuned = best[1]
+        if tuned is None:  # the library's autotuner picks the options on the first wave
+            from paper_2112_10223_gb300 import autotune
+
+            cache = args.autotune_cache or os.path.join(tempfile.mkdtemp(), "autotune.json")
+            tuner = autotune.Autotuner(cache_path=cache)
+            t0 = time.perf_counter()
+            opt = autotune.tune_batch(desc, device=dev, tuner=tuner, repeats=1)
+            tune_s = time.perf_counter() - t0
+            tuned = {f: int(getattr(opt, f)) for f in autotune.DEFAULTS}
+            rec = tuner.last
+            tune_log = {"chosen": tuned, "tuning_s": tune_s, "cached": rec["cached"],
+                        "timed_candidates": rec["timed"], "candidates": rec["candidates"]}
         opt = spk.default_options(**tuned)
         for _ in range(args.warmup):
             batch_once(spk, desc, dev, stream, opt)
@@ -846,7 +842,7 @@ def run_batch(args, world, rank, local):
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
                      "algorithmic_bytes": tot["bytes"]},
         "batch": {
-            "autotune": {"chosen": tuned, "first_wave": tune_log},
+            "autotune": tune_log,
             "instances_per_s": tot["instances"] / tot["t_batch"],
             "per_request": {"nnz_per_s": tot["nnz"] / tot["t_req"], "instances_per_s": tot["instances"] / tot["t_req"],
                             "seconds": tot["t_req"], "p50_ms": lat[len(lat) // 2] * 1e3,
@@ -1114,6 +1110,8 @@ def main():
                     help="thread-block items' accumulator: 0 automatic, 1 flat bitmap, 2 compact word table")
     ap.add_argument("--batch-count", type=int, default=4096, help="instances of the batched workload")
     ap.add_argument("--batch-mem-frac", type=float, default=0.55, help="device memory share of one wave")
+    ap.add_argument("--autotune-cache", default=None,
+                    help="autotuner cache file (default: tune afresh into a temporary cache)")
     ap.add_argument("--batch-verify", type=int, default=32,
                     help="instances per wave checked against the oracle (evenly spaced in size order)")
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests per served trace")

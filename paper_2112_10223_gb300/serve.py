@@ -10,11 +10,13 @@ one host synchronisation -- overlaps the other streams' work.  A batch stops
 taking requests once it holds enough work (input nonzeros) to amortise its
 launches, so small requests share launches and large ones run alone.
 
-Admission is by device memory.  Before planning, a request is charged an
-upper bound: its output cannot exceed its input (nnz(B) <= sum_i nnz(A_i),
-Sec. II-A) plus the planner's workspace.  After the symbolic phase the
-outputs are allocated exactly (one flat buffer per array and dtype for the
-whole batch).
+Admission is by device memory, in two steps.  A request joins a batch when
+its bound fits the budget: workspace plus an output no larger than its
+input (nnz(B) <= sum_i nnz(A_i), Sec. II-A).  After the batch's symbolic
+phase (Sec. II-D: the exact nnz(B) of every request) the charge drops to the
+outputs' exact size before they are allocated, so the memory a request does
+not need goes back to admission at once.  Outputs are one flat buffer per
+array and dtype for the whole batch.
 
 Latency is arrival to outputs complete: the completion time of a request is
 its batch's completion event, placed on a common time line with the arrival
@@ -65,9 +67,18 @@ class Request:
             va=np.asarray([a[2].data_ptr() if a[2].numel() else 0 for a in self.A], dtype=np.uint64))
 
     def bytes_bound(self) -> int:
-        """Device bytes the request may need while in flight: B <= inputs, plus workspace."""
+        """An upper bound of the device bytes the request may need while in flight: B <= inputs
+        (nnz(B) <= sum_i nnz(A_i), Sec. II-A), plus workspace."""
         sv = self.A[0][2].element_size()
-        return self.nnz_in * (4 + sv) + (self.n + 1) * 8 + 64 * self.n + 64 * self.k + 4096
+        return self.nnz_in * (4 + sv) + (self.n + 1) * 8 + self.workspace_bytes()
+
+    def workspace_bytes(self) -> int:
+        """The planner's workspace for the request (per-column and per-input tables)."""
+        return 64 * self.n + 64 * self.k + 4096
+
+    def output_bytes(self, nnz_out: int) -> int:
+        """B's exact size once the symbolic phase has given nnz(B)."""
+        return (self.n + 1) * 8 + nnz_out * (4 + self.A[0][2].element_size())
 
 
 @dataclass
@@ -137,6 +148,10 @@ class Server:
                                   np.concatenate([d["ri"] for d in desc]), np.concatenate([d["va"] for d in desc]),
                                   [r.dtype for r in reqs], stream=stream, options=self.options, device=self.device)
         nnz = np.asarray(spkadd_batch_symbolic(h), dtype=np.int64)
+        # The outputs' exact size replaces their bound in the charge before they are allocated.
+        slack = sum(r.bytes_bound() - r.workspace_bytes() - r.output_bytes(int(z)) for r, z in zip(reqs, nnz))
+        self._used -= slack
+        charged -= slack
         n1 = np.asarray([r.n + 1 for r in reqs], dtype=np.int64)
         is64 = np.asarray([r.dtype == torch.float64 for r in reqs])
         with torch.cuda.stream(stream):
@@ -188,14 +203,17 @@ class Server:
     def _run(self, requests) -> ServeStats:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         queue = collections.deque()
-        inflight = collections.deque()
-        used = 0
+        self._inflight = collections.deque()
+        self._used = 0
+        self.peak_charged = 0
         nb = 0
         torch.cuda.synchronize(self.device)
         t0_event = torch.cuda.Event(enable_timing=True)
         t0_event.record(torch.cuda.current_stream(self.device))
         t0_event.synchronize()
+        self._t0_event = t0_event
         t0 = time.perf_counter()
+        inflight = self._inflight
         while pending or queue or inflight:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
@@ -203,16 +221,16 @@ class Server:
             while inflight and inflight[0].event.query():
                 b = inflight.popleft()
                 self._finish(b, t0_event, 0.0)
-                used -= b.charged
+                self._used -= b.charged
             if queue and len(inflight) < len(self.streams):
                 take, charge, work = [], 0, 0
                 while queue and len(take) < self.max_batch:
                     if take and work + queue[0].nnz_in > self.max_batch_nnz:
                         break  # a large request runs in a batch of its own
                     c = queue[0].bytes_bound()
-                    if take and used + charge + c > self.mem_budget:
+                    if take and self._used + charge + c > self.mem_budget:
                         break
-                    if not take and inflight and used + c > self.mem_budget:
+                    if not take and inflight and self._used + c > self.mem_budget:
                         break  # wait for memory to come back
                     take.append(queue.popleft())
                     charge += c
@@ -221,8 +239,9 @@ class Server:
                     stream = self.streams[nb % len(self.streams)]
                     for r in take:
                         r.batch_id = nb
+                    self._used += charge
+                    self.peak_charged = max(self.peak_charged, self._used)
                     inflight.append(self._start(take, stream, charge))
-                    used += charge
                     nb += 1
                     continue
             # nothing to start: wait for the next arrival or the oldest batch

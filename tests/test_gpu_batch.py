@@ -173,3 +173,33 @@ def test_batch_launch_count_does_not_grow_with_problems():
         counts.append(info["kernel_launches"])
     assert counts[0] == counts[1], counts
     assert counts[0] <= 12, counts
+
+
+def test_autotuned_options_give_the_same_batch(tmp_path):
+    """The library's autotuner times candidate options on a batch, caches its choice, and the chosen options
+    give the oracle's result."""
+    from paper_2112_10223_gb300 import autotune
+
+    params = synth.batch_instance_params(12, seed=3, k_range=(2, 64), mn_range=(256, 2048), L_range=(4, 64))
+    problems_cpu = [synth.instance(p) for p in params]
+    problems = [(_dev(A), m) for A, m in problems_cpu]
+    ks, ms, ns, nnz, cps, ris, vas, dts = [], [], [], [], [], [], [], []
+    for A, m in problems:
+        ks.append(len(A))
+        ms.append(m)
+        ns.append(A[0][0].numel() - 1)
+        dts.append(A[0][2].dtype)
+        for cp, ri, va in A:
+            nnz.append(ri.numel())
+            cps.append(cp.data_ptr())
+            ris.append(ri.data_ptr() if ri.numel() else 0)
+            vas.append(va.data_ptr() if va.numel() else 0)
+    desc = dict(k=np.asarray(ks, dtype=np.int32), m=np.asarray(ms), n=np.asarray(ns), nnz=np.asarray(nnz),
+                cp=np.asarray(cps, dtype=np.uint64), ri=np.asarray(ris, dtype=np.uint64),
+                va=np.asarray(vas, dtype=np.uint64), dtypes=dts)
+    tuner = autotune.Autotuner(cache_path=str(tmp_path / "tune.json"))
+    opt = autotune.tune_batch(desc, device=DEV, tuner=tuner, repeats=1)
+    assert not tuner.last["cached"] and tuner.last["timed"] > 1
+    again = autotune.tune_batch(desc, device=DEV, tuner=autotune.Autotuner(cache_path=str(tmp_path / "tune.json")))
+    assert all(getattr(opt, f) == getattr(again, f) for f in autotune.DEFAULTS)
+    _check_batch(problems_cpu, options=opt)

@@ -67,3 +67,39 @@ def test_alone_vs_mix_digests_identical_indices(pool):
         a = alone[tag]
         assert d[0] == a[0] and d[1] == a[1], rid
         assert abs(d[2] - a[2]) <= 1e-5 * max(a[3], 1.0)
+
+
+def test_tight_budget_charges_exact_outputs(pool):
+    """A budget of a few MB: batches are split, a request's output bound is replaced by its exact size after the
+    symbolic phase, and the charge never passes the budget unless one request alone does."""
+    cpu, dev = pool
+    reqs = [Request(i, dev[i % len(dev)][0], dev[i % len(dev)][1], arrival=0.0, tag=i % len(dev))
+            for i in range(24)]
+    budget = 3 << 20
+    srv = Server(DEV, budget)
+    st = srv.run(reqs)
+    one = max(r.bytes_bound() for r in reqs)
+    assert st.batches > 1 and all(r.nnz_out >= 0 for r in reqs)
+    assert srv.peak_charged <= max(budget, one)
+
+
+def test_served_request_over_2pow31_output():
+    """One served request whose B has more than 2^31 entries (int64 column pointers through the server)."""
+    from spk_testlib import check_global_invariants, check_sampled, sample_columns
+
+    m = n = 1 << 20
+    A = synth.er(2, m, n, 1030, seed=21, dtype=torch.float32, device=torch.device(DEV))
+    got = {}
+
+    def keep(r):
+        cp, ri, va = r.out
+        check_global_invariants(A, (cp, ri, va), m)
+        cols, _ = sample_columns(A, 32, 4, seed=3)
+        last = torch.tensor([n - 2, n - 1], device=cp.device)
+        check_sampled(A, (cp, ri, va), m, torch.unique(torch.cat([cols, last])), torch.float32)
+        got["nnz"] = int(cp[-1].item())
+
+    st = Server(DEV, 1 << 37, on_done=keep).run([Request(0, A, m, arrival=0.0)])
+    assert st.requests == 1 and got["nnz"] > 2 ** 31
+    del A
+    torch.cuda.empty_cache()
