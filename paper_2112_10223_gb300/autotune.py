@@ -111,14 +111,18 @@ class Autotuner:
         return dict(e["options"]) if e else None
 
     # -- search --------------------------------------------------------------
-    def tune(self, run, dev: dict, work: dict, repeats: int = 2, timer=None, force: bool = False) -> dict:
+    def tune(self, run, dev: dict, work: dict, repeats: int = 2, timer=None, force: bool = False,
+             margin: float = 0.03) -> dict:
         """Best option values for the workload that ``run(values)`` executes.
 
         ``run`` takes a dict of option values, runs the workload once and
         returns when its work is done (synchronised).  ``timer(run, values)``
         may replace the default wall-clock timing (a warm-up run, then the
-        mean of `repeats` runs).  The result is cached under (dev, work); a
-        cached result is returned without running anything unless `force`.
+        mean of `repeats` runs).  A candidate replaces the best so far only
+        when it is faster by more than the fraction `margin`, so timing noise
+        does not move the choice away from the defaults.  The result is cached
+        under (dev, work); a cached result is returned without running
+        anything unless `force`.
         """
         if not force:
             hit = self.lookup(dev, work)
@@ -149,7 +153,7 @@ class Autotuner:
                 if not valid(cand):
                     continue
                 t = cost(cand)
-                if t < best_t:
+                if t < best_t * (1.0 - margin):
                     best, best_t = cand, t
         rec = {"options": best, "seconds": best_t, "timed": len(seen),
                "candidates": [dict(dict(k), seconds=t) for k, t in seen.items()]}

@@ -296,6 +296,10 @@ __device__ __forceinline__ const V* shfl_vptr(const V* p, int src) {
   return reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
 }
 
+// Ragged chunks whose segments average at least this many entries are walked
+// segment by segment instead of in flattened order.
+constexpr int SEG_MAJOR_MIN = 24;
+
 // A lane's segment bounds, kept from pass A for pass B when its warp walks a
 // single chunk (k <= 32 * warp groups): pass B then skips the reload.
 struct SegCache {
@@ -336,7 +340,40 @@ __device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, in
       sc.valid = true;
     }
     ChunkMap cm;
-    cm.init(beg, len, lane, min(32, k - cb));
+    const int nvalid = min(32, k - cb);
+    cm.init(beg, len, lane, nvalid);
+    if (!cm.equal && cm.total >= SEG_MAJOR_MIN * nvalid) {
+      // Ragged segments long enough to fill warp rounds: each warp walks
+      // whole segments (inputs lw, lw + per, ...), so an entry's segment is
+      // known without the per-entry search of the flattened order.
+      for (int sgi = lw; sgi < nvalid; sgi += per) {
+        const int ls = __shfl_sync(SPK_FULL, len, sgi);
+        const int32_t* p = shfl_iptr(rp, sgi);
+        const V* q = nullptr;
+        if constexpr (VALS) q = shfl_vptr(vp, sgi);
+        for (int e0 = 0; e0 < ls; e0 += 32 * U) {
+          int32_t r[U];
+          V v[U];
+#pragma unroll
+          for (int t = 0; t < U; ++t) {
+            r[t] = -1;
+            v[t] = V(0);
+            const int o = e0 + t * 32 + lane;
+            if (e0 + t * 32 < ls && o < ls) {  // (the first test is warp-uniform)
+              r[t] = __ldg(p + o);
+              if constexpr (VALS) v[t] = __ldg(q + o);
+            }
+          }
+          uint32_t tok[U];
+#pragma unroll
+          for (int t = 0; t < U; ++t) tok[t] = r[t] >= 0 ? fpre(r[t], v[t]) : 0u;
+#pragma unroll
+          for (int t = 0; t < U; ++t)
+            if (r[t] >= 0) fpost(tok[t], r[t], v[t]);
+        }
+      }
+      continue;
+    }
     if (lw * 32 * U >= cm.total) continue;  // (warp-uniform) this warp has no entries in the chunk
     for (int e0 = lw * 32 * U; e0 < cm.total; e0 += per * 32 * U) {
       int32_t r[U];

@@ -57,9 +57,10 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const int32_
 cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const Counters* ctr, int n_cols,
                             const int32_t* s, const int32_t* u, const int64_t* col_ptr, const Outs& out,
                             int warp_max, int sort_mode, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
-cudaError_t launch_num_cta(const Inputs& in, int dt, const Window* win, int n_win, const int32_t* offs,
-                           const int64_t* col_ptr, const Outs& out, int window_max, int accumulator,
-                           Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
+// f32_kinds: bit 0 = some float problem has k <= FP32_ACC_TERMS, bit 1 = some has more.
+cudaError_t launch_num_cta(const Inputs& in, int dt, int f32_kinds, const Window* win, int n_win,
+                           const int32_t* offs, const int64_t* col_ptr, const Outs& out, int window_max,
+                           int accumulator, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
 // Per-problem column pointers of B (a batch): out_cp[q][j] = col_ptr[colbase + j] - col_ptr[colbase].
 cudaError_t launch_out_colptr(const Inputs& in, const Outs& o, const int64_t* col_ptr, int sms, cudaStream_t st);
 // Per-problem nnz(B): nnz[q] = col_ptr[colbase + n] - col_ptr[colbase].

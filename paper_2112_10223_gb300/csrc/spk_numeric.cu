@@ -97,6 +97,16 @@ __device__ __forceinline__ uint32_t own_word_mask(const uint32_t* summ, int w0, 
   return per == 32 ? all : (all & ((1u << per) - 1u));
 }
 
+// Item filter of a launch that covers only some problems of a batch:
+// 0 float, 1 double, 2 float with k <= FP32_ACC_TERMS, 3 float with more.
+__device__ __forceinline__ bool item_selected(int sel, const Inst* I) {
+  if (sel == 1) return I->dtype == 1;
+  if (I->dtype != 0) return false;
+  if (sel == 2) return I->k <= FP32_ACC_TERMS;
+  if (sel == 3) return I->k > FP32_ACC_TERMS;
+  return true;
+}
+
 // One item (a CTA-class column or a heavy column's row window [r_lo, r_hi),
 // Alg. 8: B(r1:r2, j) <- HashAdd(A_1(r1:r2, j), ..., A_k(r1:r2, j))).
 template <typename V, typename A, int BLOCK, int U>
@@ -430,7 +440,7 @@ __global__ void __launch_bounds__(BLOCK) k_num_compact(Inputs in, const Window* 
     if (wi + (int)gridDim.x < nwin) Wn = win[wi + gridDim.x];
     const int q = inst_of(in, W.col);
     const Inst* I = in.inst + q;
-    if (only_dtype >= 0 && I->dtype != only_dtype) continue;
+    if (only_dtype >= 0 && !item_selected(only_dtype, I)) continue;
     const int64_t out = col_ptr[W.col] - (in.col_inst ? col_ptr[I->colbase] : 0) + W.out_off;
     compact_item<V, A, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
                               slab_log2, ctr_w);
@@ -470,7 +480,7 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
     if (wi + (int)gridDim.x < nwin) Wn = win[wi + gridDim.x];
     const int q = inst_of(in, W.col);
     const Inst* I = in.inst + q;
-    if (only_dtype >= 0 && I->dtype != only_dtype) continue;
+    if (only_dtype >= 0 && !item_selected(only_dtype, I)) continue;
     const int64_t out = col_ptr[W.col] - (in.col_inst ? col_ptr[I->colbase] : 0) + W.out_off;
     bitmap_item<V, A, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
                              slab_log2, ctr_w);
@@ -567,27 +577,28 @@ static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_w
                       only_dtype, ctr_w, dev, st);
 }
 
-cudaError_t launch_num_cta(const Inputs& in, int dt, const Window* win, int n_win, const int32_t* offs,
-                           const int64_t* col_ptr, const Outs& out, int window_max, int accumulator, Counters* ctr_w,
-                           const DeviceInfo& dev, cudaStream_t st) {
+cudaError_t launch_num_cta(const Inputs& in, int dt, int f32_kinds, const Window* win, int n_win,
+                           const int32_t* offs, const int64_t* col_ptr, const Outs& out, int window_max,
+                           int accumulator, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
   if (n_win <= 0) return cudaSuccess;
   // Float values are summed in float while no output entry can have more
   // than FP32_ACC_TERMS terms (k <= 167: the error bound of the fp32
-  // tolerance holds), else in double.
-  const bool wide = in.kmax > FP32_ACC_TERMS;
-  auto launch_f32 = [&](int only) {
-    return wide ? launch_num_cta_t<0, true>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, only, ctr_w,
-                                            dev, st)
-                : launch_num_cta_t<0, false>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, only, ctr_w,
-                                             dev, st);
-  };
-  if (dt == 0) return launch_f32(-1);
-  if (dt == 1)
-    return launch_num_cta_t<1, false>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st);
-  // Mixed batch: one launch per dtype, each skipping the other dtype's items.
-  cudaError_t e = launch_f32(0);
-  if (e == cudaSuccess)
-    e = launch_num_cta_t<1, false>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, 1, ctr_w, dev, st);
+  // tolerance holds), else in double.  A batch holding both kinds of float
+  // problems runs one launch for each (f32_kinds: bit 0 k <= 167, bit 1 more).
+  const bool narrow = f32_kinds & 1, wide = f32_kinds & 2;
+  cudaError_t e = cudaSuccess;
+  if (dt != 1) {
+    const int sel_n = (dt == 2 || wide) ? 2 : -1, sel_w = (dt == 2 || narrow) ? 3 : -1;
+    if (narrow)
+      e = launch_num_cta_t<0, false>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, sel_n, ctr_w, dev,
+                                     st);
+    if (e == cudaSuccess && wide)
+      e = launch_num_cta_t<0, true>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, sel_w, ctr_w, dev,
+                                    st);
+  }
+  if (e == cudaSuccess && dt != 0)
+    e = launch_num_cta_t<1, false>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, dt == 2 ? 1 : -1,
+                                   ctr_w, dev, st);
   return e;
 }
 

@@ -139,14 +139,15 @@ __global__ void __launch_bounds__(BLOCK, BLOCK >= 1024 ? 1 : 4) k_sym_heavy(Inpu
   const int n_big = ctr->n_big;
   const int ncols = n_big + ctr->n_heavy;
   const int slab_rows = 1 << slab_log2;
-  __shared__ int s_next;
-  // Columns are handed out by a work counter, the largest list first.
-  for (;;) {
-    if (threadIdx.x == 0) s_next = atomicAdd(&ctr_w->heavy_next, 1);
-    __syncthreads();
-    const int c = s_next;
-    __syncthreads();
+  // Columns are handed out by a work counter, the largest list first; the
+  // next column's ticket is taken while the current one runs.
+  __shared__ int s_tk[2];
+  if (threadIdx.x == 0) s_tk[0] = atomicAdd(&ctr_w->heavy_next, 1);
+  __syncthreads();
+  for (int it = 0;; ++it) {
+    const int c = s_tk[it & 1];
     if (c >= ncols) break;
+    if (threadIdx.x == 0) s_tk[(it + 1) & 1] = atomicAdd(&ctr_w->heavy_next, 1);
     const int g = c < n_big ? list[in.ncols + c] : list[c - n_big];
     const Inst* I = in.inst + inst_of(in, g);
     const int k = I->k, off = I->ptr_off, m = I->m, j = g - I->colbase;
@@ -178,7 +179,41 @@ __global__ void __launch_bounds__(BLOCK, BLOCK >= 1024 ? 1 : 4) k_sym_heavy(Inpu
           rp = ri + b;
         }
         ChunkMap cm;
-        cm.init(beg, len, lane, min(32, k - cb));
+        const int nvalid = min(32, k - cb);
+        cm.init(beg, len, lane, nvalid);
+        // Sets the row bits of U rows (r < 0: none), then the summary marks they call for.
+        auto set_rows = [&](const int32_t (&r)[U]) {
+          bool fresh[U];
+#pragma unroll
+          for (int t = 0; t < U; ++t) {
+            const uint32_t rr = (uint32_t)(r[t] - lo);
+            fresh[t] = r[t] >= 0 && rr < width && set_row_bit(bm, rr);
+          }
+#pragma unroll
+          for (int t = 0; t < U; ++t)
+            if (fresh[t]) {
+              const uint32_t w = (uint32_t)(r[t] - lo) >> 6;
+              atomicOr(&summ[w >> 5], 1u << (w & 31));
+            }
+        };
+        if (!cm.equal && cm.total >= SEG_MAJOR_MIN * nvalid) {
+          // Long ragged segments: each warp walks whole segments (no per-entry search).
+          for (int sgi = lw; sgi < nvalid; sgi += wpg) {
+            const int ls = __shfl_sync(SPK_FULL, len, sgi);
+            const int32_t* p = reinterpret_cast<const int32_t*>(
+                __shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(rp), sgi));
+            for (int e0 = 0; e0 < ls; e0 += 32 * U) {
+              int32_t r[U];
+#pragma unroll
+              for (int t = 0; t < U; ++t) {
+                const int o = e0 + t * 32 + lane;
+                r[t] = (e0 + t * 32 < ls && o < ls) ? __ldg(p + o) : -1;
+              }
+              set_rows(r);
+            }
+          }
+          continue;
+        }
         if (lw * 32 * U >= cm.total) continue;  // (warp-uniform) no entries for this warp
         for (int e0 = lw * 32 * U; e0 < cm.total; e0 += wpg * 32 * U) {
           int32_t r[U];
@@ -194,18 +229,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK >= 1024 ? 1 : 4) k_sym_heavy(Inpu
             if (e < cm.total) r[t] = __ldg(p + o);
           }
           // All bit sets of the round first, then the summary marks they call for.
-          bool fresh[U];
-#pragma unroll
-          for (int t = 0; t < U; ++t) {
-            const uint32_t rr = (uint32_t)(r[t] - lo);
-            fresh[t] = r[t] >= 0 && rr < width && set_row_bit(bm, rr);
-          }
-#pragma unroll
-          for (int t = 0; t < U; ++t)
-            if (fresh[t]) {
-              const uint32_t w = (uint32_t)(r[t] - lo) >> 6;
-              atomicOr(&summ[w >> 5], 1u << (w & 31));
-            }
+          set_rows(r);
         }
       }
       __syncthreads();
@@ -333,14 +357,15 @@ __global__ void __launch_bounds__(BLOCK) k_sym_heavy_compact(Inputs in, const in
   const int ncols = n_big + ctr->n_heavy;
   const int slab_rows = 1 << slab_log2;
   const int capw = cap - 32;  // a sub-range starts below capw words: it ends below cap
-  __shared__ int s_next;
-  // Columns are handed out by a work counter, the largest list first.
-  for (;;) {
-    if (threadIdx.x == 0) s_next = atomicAdd(&ctr_w->heavy_next, 1);
-    __syncthreads();
-    const int c = s_next;
-    __syncthreads();
+  // Columns are handed out by a work counter, the largest list first; the
+  // next column's ticket is taken while the current one runs.
+  __shared__ int s_tk[2];
+  if (threadIdx.x == 0) s_tk[0] = atomicAdd(&ctr_w->heavy_next, 1);
+  __syncthreads();
+  for (int it = 0;; ++it) {
+    const int c = s_tk[it & 1];
     if (c >= ncols) break;
+    if (threadIdx.x == 0) s_tk[(it + 1) & 1] = atomicAdd(&ctr_w->heavy_next, 1);
     const int g = c < n_big ? list[in.ncols + c] : list[c - n_big];
     const Inst* I = in.inst + inst_of(in, g);
     const int k = I->k, off = I->ptr_off, m = I->m, j = g - I->colbase;

@@ -62,3 +62,18 @@ def test_candidates_respect_the_option_ranges():
     assert not autotune.valid({"warp_max": 512, "cta_max": 256})
     for knob, values in autotune.SPACE.items():
         assert autotune.DEFAULTS[knob] in values
+
+
+def test_gains_within_the_margin_keep_the_defaults(tmp_path):
+    """A candidate 1 % faster than the defaults is noise under a 3 % margin; 10 % faster is taken."""
+    def timer_small(run, values):
+        return 0.99 if values["block_accumulator"] == 2 else 1.0
+
+    t = autotune.Autotuner(cache_path=str(tmp_path / "m.json"))
+    assert t.tune(lambda v: None, DEV, WORK, timer=timer_small) == autotune.DEFAULTS
+
+    def timer_big(run, values):
+        return 0.9 if values["block_accumulator"] == 2 else 1.0
+
+    assert t.tune(lambda v: None, DEV, WORK, timer=timer_big, force=True) == dict(autotune.DEFAULTS,
+                                                                                 block_accumulator=2)
