@@ -301,7 +301,7 @@ def spkadd_destroy(h: Handle) -> None:
 
 
 def spkadd(A, m: int, dtype=None, stream=None, options: Options | None = None, info: bool = False,
-           method: str = "onepass"):
+           method: str = "twopass"):
     """B = sum of the inputs; returns (col_ptr int64, row_idx int32, val) CUDA tensors.
 
     method "onepass": spkadd_onepass into buffers of sum nnz(A_i) entries

@@ -121,7 +121,7 @@ struct spkadd_handle {
   int64_t ncols = 0;        // columns of all problems
   int64_t nnz_in = 0;
   int dt_mode = 0;          // 0 = all float, 1 = all double, 2 = mixed
-  int f32_kinds = 0;        // bit 0: a float problem with k <= FP32_ACC_TERMS; bit 1: one with more
+  int f32_kinds = 0;        // float problems held: bit 0 k <= 167, bit 1 167 < k <= FP32_PHASED_MAX_K, bit 2 larger
   spkadd_dtype dt0 = SPKADD_F64;
   cudaStream_t st = nullptr;
   spkadd_options opt{};
@@ -260,7 +260,8 @@ static spkadd_status plan_problems(spkadd_handle** hp, bool batch, int count, co
     if (As[q][0].m > mmax) mmax = As[q][0].m;
     if (ks[q] > kmax) kmax = ks[q];
     (dts[q] == SPKADD_F64 ? any64 : any32) = true;
-    if (dts[q] == SPKADD_F32) f32_kinds |= ks[q] > spk::FP32_ACC_TERMS ? 2 : 1;
+    if (dts[q] == SPKADD_F32)
+      f32_kinds |= ks[q] <= spk::FP32_ACC_TERMS ? 1 : (ks[q] <= spk::FP32_PHASED_MAX_K ? 2 : 4);
     win_cap += window_bound(As[q][0].m, As[q][0].n, nz, o);
   }
   if (total_k >= INT32_MAX || ncols >= INT32_MAX || win_cap >= INT32_MAX) return SPKADD_ERR_OVERFLOW;
@@ -513,7 +514,7 @@ static spkadd_status run_numeric(spkadd_handle* h, const spk::Outs& out) {
     ce = spk::launch_num_cta(h->in, h->dt_mode, h->f32_kinds, h->d_win, cta_items, h->d_offs, h->d_colptr, out,
                              h->opt.window_max > h->opt.cta_max ? h->opt.window_max : h->opt.cta_max,
                              h->opt.block_accumulator, h->d_ctr, h->dev, h->st);
-  h->launches += (cta_items > 0) * ((h->dt_mode != 0) + (h->f32_kinds & 1) + ((h->f32_kinds >> 1) & 1));
+  h->launches += (cta_items > 0) * ((h->dt_mode != 0) + (h->dt_mode != 1 ? __builtin_popcount(h->f32_kinds) : 0));
   if (ce == cudaSuccess && h->h_ctr.n_warp > 0)
     ce = spk::launch_num_warp(h->in, h->dt_mode, h->d_wl, h->d_ctr, h->h_ctr.n_warp, h->d_s, h->d_u, h->d_colptr,
                               out, h->opt.warp_max, h->opt.sort_mode, h->d_ctr, h->dev, h->st);

@@ -44,12 +44,26 @@ struct Counters {
   int32_t pad[3];
 };
 
-// Float inputs are accumulated in float while no output entry can collect more
-// terms than this (k <= 167): recursive summation errs by at most
-// (t - 1) 2^-24 sum|terms| plus one final rounding, within 1e-5 sum|terms|.
-// Beyond it the thread-block accumulators use double; warp columns always sum
-// a row's run in double.
+// Float sums.  A float sum of t terms, in any order, errs by at most
+// (t - 1) 2^-24 sum|terms| (first order), within 1e-5 sum|terms| for
+// t <= FP32_ACC_TERMS.  Thread-block accumulators of problems with k <= 167
+// sum in float, and so do those slabs of larger problems whose entries
+// leave no row more than 167 terms (a row's terms number at most
+// s - u + 1 for s entries on u distinct rows).  Other slabs of problems
+// with k <= FP32_PHASED_MAX_K sum in phases of FP32_PHASE_INPUTS inputs:
+// each phase in float, its partial sums then added in float into B's
+// values, so an entry collects at most 128 terms in a phase and at most
+// ceil(k / 128) phase sums, and its error stays below
+// (127 + ceil(k / 128) - 1) 2^-24 sum|terms| <= 166 * 2^-24 sum|terms|.
+// Beyond FP32_PHASED_MAX_K the accumulators are double.  Warp columns
+// always sum a row's run in double.
 constexpr int FP32_ACC_TERMS = 167;
+constexpr int FP32_PHASE_INPUTS = 128;  // whole 32-input chunks, one per warp group of a 256-thread block
+constexpr int FP32_PHASED_MAX_K = 4992;
+static_assert((FP32_PHASE_INPUTS - 1) + (FP32_PHASED_MAX_K / FP32_PHASE_INPUTS - 1) <= FP32_ACC_TERMS - 1,
+              "phased float sums must stay within the float error bound");
+static_assert(FP32_PHASE_INPUTS % 32 == 0, "phases are whole 32-input chunks");
+
 
 // Heavy columns above this summed input count are listed apart and handed out
 // first (largest work first keeps one huge R-MAT column from finishing last).
@@ -307,19 +321,20 @@ struct SegCache {
   bool valid;
 };
 
+// Inputs [k_lo, k) of the item (k_lo a multiple of 32).
 template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename FPre, typename FPost>
-__device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, int off, SegF& seg, FPre& fpre,
-                                                     FPost& fpost, SegCache& sc) {
+__device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k_lo, int k, int off, SegF& seg,
+                                                     FPre& fpre, FPost& fpost, SegCache& sc) {
   constexpr int NW = BLOCK / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // The chunks of 32 inputs run side by side: `groups` of `per` warps, group
   // g taking chunks g, g + groups, ... (all chunks' loads are in flight at once).
-  const int nch = (k + 31) >> 5;
+  const int nch = (k - k_lo + 31) >> 5;
   const int groups = min(nch, NW);
   const int per = NW / groups;
   const int gid = wid / per, lw = wid - gid * per;
   if (gid >= groups) return;  // (warp-uniform) spare warps
-  for (int cb = gid * 32; cb < k; cb += groups * 32) {
+  for (int cb = k_lo + gid * 32; cb < k; cb += groups * 32) {
     const int i = cb + lane;
     int beg = 0, len = 0;
     const int32_t* rp = nullptr;
@@ -402,6 +417,12 @@ __device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, in
         if (r[t] >= 0) fpost(tok[t], r[t], v[t]);
     }
   }
+}
+
+template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename FPre, typename FPost>
+__device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, int off, SegF& seg, FPre& fpre,
+                                                     FPost& fpost, SegCache& sc) {
+  block_for_each_entry<VALS, V, BLOCK, U>(in, 0, k, off, seg, fpre, fpost, sc);
 }
 
 }  // namespace spk

@@ -57,7 +57,7 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const int32_
 cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const Counters* ctr, int n_cols,
                             const int32_t* s, const int32_t* u, const int64_t* col_ptr, const Outs& out,
                             int warp_max, int sort_mode, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
-// f32_kinds: bit 0 = some float problem has k <= FP32_ACC_TERMS, bit 1 = some has more.
+// f32_kinds: float problems held: bit 0 k <= FP32_ACC_TERMS, bit 1 up to FP32_PHASED_MAX_K, bit 2 larger.
 cudaError_t launch_num_cta(const Inputs& in, int dt, int f32_kinds, const Window* win, int n_win,
                            const int32_t* offs, const int64_t* col_ptr, const Outs& out, int window_max,
                            int accumulator, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);

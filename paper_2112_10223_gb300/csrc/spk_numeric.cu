@@ -98,18 +98,48 @@ __device__ __forceinline__ uint32_t own_word_mask(const uint32_t* summ, int w0, 
 }
 
 // Item filter of a launch that covers only some problems of a batch:
-// 0 float, 1 double, 2 float with k <= FP32_ACC_TERMS, 3 float with more.
+// 0 float, 1 double, 2 float with k <= FP32_ACC_TERMS, 3 float with
+// FP32_ACC_TERMS < k <= FP32_PHASED_MAX_K, 4 float with larger k.
 __device__ __forceinline__ bool item_selected(int sel, const Inst* I) {
   if (sel == 1) return I->dtype == 1;
   if (I->dtype != 0) return false;
   if (sel == 2) return I->k <= FP32_ACC_TERMS;
-  if (sel == 3) return I->k > FP32_ACC_TERMS;
+  if (sel == 3) return I->k > FP32_ACC_TERMS && I->k <= FP32_PHASED_MAX_K;
+  if (sel == 4) return I->k > FP32_PHASED_MAX_K;
+  return true;
+}
+
+// Pass B of an item's slab: every entry's value added at its rank.  Without
+// phases the sums stay in acc for the caller's write (returns false).
+// PHASED (float sums of problems with k > FP32_ACC_TERMS): a slab whose
+// s_ent entries on slab_u rows can give a row more than FP32_ACC_TERMS
+// terms runs its inputs in phases of FP32_PHASE_INPUTS; after each phase the
+// slab's first `lim` partial sums are added into B's values (the first phase
+// stores them) and acc is zeroed (returns true: the values are written).
+template <typename V, typename A, bool PHASED, int BLOCK, int U, typename SegF, typename FAdd>
+__device__ __forceinline__ bool add_values(const Inputs& in, int k, int off, SegF& seg, FAdd& add, SegCache& sc,
+                                           A* acc, V* oval, int slab_u, int lim, int s_ent) {
+  auto none = [](uint32_t, int32_t, V) {};
+  if (!PHASED || s_ent - slab_u < FP32_ACC_TERMS) {
+    block_for_each_entry<true, V, BLOCK, U>(in, 0, k, off, seg, add, none, sc);
+    return false;
+  }
+  for (int p0 = 0; p0 < k; p0 += FP32_PHASE_INPUTS) {
+    SegCache fresh{0, 0, false};  // a phase's chunks differ from pass A's
+    block_for_each_entry<true, V, BLOCK, U>(in, p0, min(k, p0 + FP32_PHASE_INPUTS), off, seg, add, none, fresh);
+    __syncthreads();
+    for (int q = threadIdx.x; q < slab_u; q += BLOCK) {
+      if (q < lim) oval[q] = p0 == 0 ? (V)acc[q] : oval[q] + (V)acc[q];
+      acc[q] = A(0);
+    }
+    __syncthreads();
+  }
   return true;
 }
 
 // One item (a CTA-class column or a heavy column's row window [r_lo, r_hi),
 // Alg. 8: B(r1:r2, j) <- HashAdd(A_1(r1:r2, j), ..., A_k(r1:r2, j))).
-template <typename V, typename A, int BLOCK, int U>
+template <typename V, typename A, bool PHASED, int BLOCK, int U>
 __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, const Inst* I, const int32_t* offs,
                                             int32_t* __restrict__ out_row, V* __restrict__ out_val,
                                             const BitmapSmem& sm, int slab_log2, Counters* ctr_w) {
@@ -147,8 +177,10 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
     };
     // Pass A: row bits (rows outside the slab are ignored: they cannot occur
     // for valid inputs, and shared-memory accesses stay in bounds).
+    int n_ent = 0;  // PHASED: entries this thread met in the slab
     auto setbit = [&](int32_t r, V) -> uint32_t {
       const uint32_t rr = (uint32_t)(r - lo);
+      if constexpr (PHASED) n_ent += rr < width;
       return (rr < width && set_row_bit(sm.bm, rr)) ? 1u : 0u;
     };
     auto mark_word = [&](uint32_t fresh, int32_t r, V) {
@@ -160,6 +192,8 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
     SegCache sc{0, 0, false};
     block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, setbit, mark_word, sc);
     __syncthreads();
+    int s_ent = 0;
+    if constexpr (PHASED) block_excl_scan<BLOCK>(n_ent, reinterpret_cast<int*>(sm.red), &s_ent);
     // Rank prefix: thread t owns bitmap words [t*per, t*per + per); their
     // non-empty ones are the set bits of `mine` (kept for the clear below).
     const int nwords = (int)((width + 63) >> 6);
@@ -203,8 +237,10 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
         }
         return 0u;
       };
-      auto none = [](uint32_t, int32_t, V) {};
-      block_for_each_entry<true, V, BLOCK, U>(in, k, off, seg, add, none, sc);
+      // Ranks past the symbolic count are never written (B holds W.u rows
+      // here); they can only arise if the inputs changed between the passes.
+      const bool written = add_values<V, A, PHASED, BLOCK, U>(in, k, off, seg, add, sc, acc, out_val + u_done, slab_u,
+                                                              min(slab_u, W.u - u_done), s_ent);
       // Rows in rank order: one thread per non-empty word.
       for (int p = threadIdx.x; p < slab_ne; p += BLOCK) {
         const int w = sm.nel[p];
@@ -213,15 +249,13 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
         for (unsigned long long bits = sm.bm[w]; bits; bits &= bits - 1) sm.rows[q++] = rbase + __ffsll(bits) - 1;
       }
       __syncthreads();
-      // Coalesced write of the slab's rows and values.  Ranks past the
-      // symbolic count are never written (B holds W.u rows here); they can
-      // only arise if the inputs changed between the passes.
+      // Coalesced write of the slab's rows and values.
       const int lim = min(slab_u, W.u - u_done);
       int32_t* orow = out_row + u_done;
       V* oval = out_val + u_done;
       for (int q = threadIdx.x; q < lim; q += BLOCK) {
         orow[q] = sm.rows[q];
-        oval[q] = (V)acc[q];
+        if (!written) oval[q] = (V)acc[q];
       }
       u_done += slab_u;
     }
@@ -269,7 +303,7 @@ __device__ __forceinline__ int compact_index(const CompactSmem& sm, uint32_t w) 
   return (int)sm.spre[x] + __popc(sm.summ[x] & ((1u << (w & 31)) - 1u));
 }
 
-template <typename V, typename A, int BLOCK, int U>
+template <typename V, typename A, bool PHASED, int BLOCK, int U>
 __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, const Inst* I, const int32_t* offs,
                                              int32_t* __restrict__ out_row, V* __restrict__ out_val,
                                              const CompactSmem& sm, int slab_log2, Counters* ctr_w) {
@@ -305,9 +339,11 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
     };
     auto none = [](uint32_t, int32_t, V) {};
     // Pass A1: summary bits (a read first: dense items hit few words often).
+    int n_ent = 0;  // PHASED: entries this thread met in the slab
     auto mark = [&](int32_t r, V) -> uint32_t {
       const uint32_t rr = (uint32_t)(r - lo);
       if (rr < width) {
+        if constexpr (PHASED) ++n_ent;
         const uint32_t w = rr >> 5, bit = 1u << (w & 31);
         if (!(sm.summ[w >> 5] & bit)) atomicOr(&sm.summ[w >> 5], bit);
       }
@@ -316,6 +352,8 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
     SegCache sc{0, 0, false};
     block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, mark, none, sc);
     __syncthreads();
+    int s_ent = 0;
+    if constexpr (PHASED) block_excl_scan<BLOCK>(n_ent, sm.red, &s_ent);
     // Rank 1: thread t owns summary words [t*ps, t*ps + ps).
     const int nwords = (int)((width + 31) >> 5);
     const int nsw = (nwords + 31) >> 5;
@@ -382,11 +420,12 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
         }
         return 0u;
       };
-      block_for_each_entry<true, V, BLOCK, U>(in, k, off, seg, add, none, sc);
+      // Ranks past the symbolic count are never written (B holds W.u rows here).
+      const bool written = add_values<V, A, PHASED, BLOCK, U>(in, k, off, seg, add, sc, acc, out_val + u_done, slab_u,
+                                                              min(slab_u, W.u - u_done), s_ent);
       __syncthreads();
       // Rows straight from the words (consecutive words go to consecutive
-      // ranks), values copied out coalesced.  Ranks past the symbolic count
-      // are never written (B holds W.u rows here).
+      // ranks), values copied out coalesced.
       const int lim = min(slab_u, W.u - u_done);
       int32_t* orow = out_row + u_done;
       V* oval = out_val + u_done;
@@ -398,7 +437,8 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
           ++q;
         }
       }
-      for (int q = threadIdx.x; q < lim; q += BLOCK) oval[q] = (V)acc[q];
+      if (!written)
+        for (int q = threadIdx.x; q < lim; q += BLOCK) oval[q] = (V)acc[q];
       u_done += slab_u;
       __syncthreads();
     }
@@ -411,13 +451,13 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
   if (threadIdx.x == 0 && (bad || u_done != W.u)) atomicOr(&ctr_w->err, ERR_INTERNAL);
 }
 
-template <int DT, bool WIDE, int BLOCK, int U>
+template <int DT, int ACC, int BLOCK, int U>
 __global__ void __launch_bounds__(BLOCK) k_num_compact(Inputs in, const Window* __restrict__ win, int nwin,
                                                        const int32_t* __restrict__ offs,
                                                        const int64_t* __restrict__ col_ptr, Outs o, int slab_log2,
                                                        int umax, int only_dtype, Counters* ctr_w) {
   using V = typename std::conditional<DT == 1, double, float>::type;
-  using A = typename std::conditional<DT == 1 || WIDE, double, float>::type;  // accumulator
+  using A = typename std::conditional<DT == 1 || ACC == 2, double, float>::type;  // accumulator
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int red[BLOCK / 32 + 1];
   CompactSmem sm;
@@ -442,20 +482,20 @@ __global__ void __launch_bounds__(BLOCK) k_num_compact(Inputs in, const Window* 
     const Inst* I = in.inst + q;
     if (only_dtype >= 0 && !item_selected(only_dtype, I)) continue;
     const int64_t out = col_ptr[W.col] - (in.col_inst ? col_ptr[I->colbase] : 0) + W.out_off;
-    compact_item<V, A, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
+    compact_item<V, A, ACC == 1, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
                               slab_log2, ctr_w);
   }
 }
 
 // DT: 0 = float values, 1 = double values.  A batch mixing both runs the
 // kernel once per dtype; only_dtype >= 0 then skips the other dtype's items.
-template <int DT, bool WIDE, int BLOCK, int U>
+template <int DT, int ACC, int BLOCK, int U>
 __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* __restrict__ win, int nwin,
                                                       const int32_t* __restrict__ offs,
                                                       const int64_t* __restrict__ col_ptr, Outs o, int slab_log2,
                                                       int umax, int only_dtype, Counters* ctr_w) {
   using V = typename std::conditional<DT == 1, double, float>::type;
-  using A = typename std::conditional<DT == 1 || WIDE, double, float>::type;  // accumulator
+  using A = typename std::conditional<DT == 1 || ACC == 2, double, float>::type;  // accumulator
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ unsigned long long red[BLOCK / 32 + 1];
   BitmapSmem sm;
@@ -482,7 +522,7 @@ __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* _
     const Inst* I = in.inst + q;
     if (only_dtype >= 0 && !item_selected(only_dtype, I)) continue;
     const int64_t out = col_ptr[W.col] - (in.col_inst ? col_ptr[I->colbase] : 0) + W.out_off;
-    bitmap_item<V, A, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
+    bitmap_item<V, A, ACC == 1, BLOCK, U>(in, W, I, offs, out_row_of(o, q) + out, static_cast<V*>(out_val_of(o, q)) + out, sm,
                              slab_log2, ctr_w);
   }
 }
@@ -549,11 +589,11 @@ static cudaError_t launch_items(K kern, int block, int blocks_per_sm, const Inpu
 // Automatic takes the compact table when more of its blocks are resident per
 // SM (the flat bitmap's size follows the slab, the table's follows umax):
 // items are latency chains, so items in flight per SM decide the rate.
-template <int DT, bool WIDE>
+template <int DT, int ACC>
 static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_win, const int32_t* offs,
                                     const int64_t* col_ptr, const Outs& out, int umax, int accumulator,
                                     int only_dtype, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
-  constexpr size_t VS = (DT == 1 || WIDE) ? 8 : 4;  // accumulator bytes
+  constexpr size_t VS = (DT == 1 || ACC == 2) ? 8 : 4;  // accumulator bytes
   int slab_log2 = 10;
   while (slab_log2 < NUM_SLAB_LOG2_MAX && ((int64_t)1 << slab_log2) < (int64_t)in.mmax) ++slab_log2;
   const size_t sf = bitmap_smem_bytes(slab_log2, umax, VS), sc = compact_smem_bytes(slab_log2, umax, VS);
@@ -561,19 +601,19 @@ static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_w
   // (measured best, with 8 entries per lane and round); a bitmap that fills
   // the SM gets one 1024-thread block.
   const bool small = sf <= (size_t)dev.smem_per_sm / 2 - 2048;
-  const void* kf = small ? (const void*)k_num_bitmap<DT, WIDE, 256, 8> : (const void*)k_num_bitmap<DT, WIDE, 1024, 4>;
-  const void* kc = (const void*)k_num_compact<DT, WIDE, 256, 8>;
+  const void* kf = small ? (const void*)k_num_bitmap<DT, ACC, 256, 8> : (const void*)k_num_bitmap<DT, ACC, 1024, 4>;
+  const void* kc = (const void*)k_num_compact<DT, ACC, 256, 8>;
   int bf = 0, bc = 0;
   if (accumulator != 2 && sf <= (size_t)dev.smem_optin) bf = resident_blocks(kf, small ? 256 : 1024, sf);
   if (accumulator != 1 && sc <= (size_t)dev.smem_optin) bc = resident_blocks(kc, 256, sc);
   const bool compact = accumulator == 2 || (accumulator == 0 && bc > bf);
   if (compact)
-    return launch_items(k_num_compact<DT, WIDE, 256, 8>, 256, bc, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sc,
+    return launch_items(k_num_compact<DT, ACC, 256, 8>, 256, bc, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sc,
                         only_dtype, ctr_w, dev, st);
   if (small)
-    return launch_items(k_num_bitmap<DT, WIDE, 256, 8>, 256, bf, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sf,
+    return launch_items(k_num_bitmap<DT, ACC, 256, 8>, 256, bf, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sf,
                         only_dtype, ctr_w, dev, st);
-  return launch_items(k_num_bitmap<DT, WIDE, 1024, 4>, 1024, bf, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sf,
+  return launch_items(k_num_bitmap<DT, ACC, 1024, 4>, 1024, bf, in, win, n_win, offs, col_ptr, out, slab_log2, umax, sf,
                       only_dtype, ctr_w, dev, st);
 }
 
@@ -581,24 +621,25 @@ cudaError_t launch_num_cta(const Inputs& in, int dt, int f32_kinds, const Window
                            const int32_t* offs, const int64_t* col_ptr, const Outs& out, int window_max,
                            int accumulator, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
   if (n_win <= 0) return cudaSuccess;
-  // Float values are summed in float while no output entry can have more
-  // than FP32_ACC_TERMS terms (k <= 167: the error bound of the fp32
-  // tolerance holds), else in double.  A batch holding both kinds of float
-  // problems runs one launch for each (f32_kinds: bit 0 k <= 167, bit 1 more).
-  const bool narrow = f32_kinds & 1, wide = f32_kinds & 2;
+  // Float problems: k <= FP32_ACC_TERMS sum in float, up to
+  // FP32_PHASED_MAX_K in float by phases, beyond in double; each kind that
+  // the batch holds gets its own launch (f32_kinds bit 0, 1, 2), which skips
+  // the other problems' items when the batch holds more than one kind.
+  const int kinds = (dt != 1 ? f32_kinds : 0) + (dt != 0 ? 8 : 0);
+  const bool alone = __builtin_popcount(kinds) == 1;
   cudaError_t e = cudaSuccess;
-  if (dt != 1) {
-    const int sel_n = (dt == 2 || wide) ? 2 : -1, sel_w = (dt == 2 || narrow) ? 3 : -1;
-    if (narrow)
-      e = launch_num_cta_t<0, false>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, sel_n, ctr_w, dev,
-                                     st);
-    if (e == cudaSuccess && wide)
-      e = launch_num_cta_t<0, true>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, sel_w, ctr_w, dev,
-                                    st);
-  }
-  if (e == cudaSuccess && dt != 0)
-    e = launch_num_cta_t<1, false>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, dt == 2 ? 1 : -1,
-                                   ctr_w, dev, st);
+  if (kinds & 1)
+    e = launch_num_cta_t<0, 0>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, alone ? -1 : 2, ctr_w,
+                               dev, st);
+  if (e == cudaSuccess && (kinds & 2))
+    e = launch_num_cta_t<0, 1>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, alone ? -1 : 3, ctr_w,
+                               dev, st);
+  if (e == cudaSuccess && (kinds & 4))
+    e = launch_num_cta_t<0, 2>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, alone ? -1 : 4, ctr_w,
+                               dev, st);
+  if (e == cudaSuccess && (kinds & 8))
+    e = launch_num_cta_t<1, 0>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, alone ? -1 : 1, ctr_w,
+                               dev, st);
   return e;
 }
 

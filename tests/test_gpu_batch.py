@@ -203,3 +203,21 @@ def test_autotuned_options_give_the_same_batch(tmp_path):
     again = autotune.tune_batch(desc, device=DEV, tuner=autotune.Autotuner(cache_path=str(tmp_path / "tune.json")))
     assert all(getattr(opt, f) == getattr(again, f) for f in autotune.DEFAULTS)
     _check_batch(problems_cpu, options=opt)
+
+
+def test_float_sums_in_phases_and_in_double_in_one_batch():
+    """One batch holding fp32 problems with k <= 167 (float sums), 167 < k <= 6912 (float sums in phases of
+    96 inputs, including a ragged last phase) and k > 6912 (double sums), plus an fp64 problem: four launches
+    of the thread-block kernels, each problem within the fp32 bound of 1e-5 * sum|terms| per entry."""
+    problems = [
+        (synth.spgemm_like(40, 512, 24, 16, seed=90, dtype=F32), 512),     # float, one phase
+        (synth.spgemm_like(168, 512, 24, 16, seed=91, dtype=F32), 512),    # two phases: 96 + 72
+        (synth.spgemm_like(300, 256, 20, 8, seed=92, dtype=F32), 256),     # four phases, last one 12 inputs
+        (synth.spgemm_like(6920, 64, 3, 1, seed=93, dtype=F32), 64),       # double accumulators
+        (synth.spgemm_like(200, 512, 24, 16, seed=94, dtype=F64), 512),
+    ]
+    opt = spk.default_options(warp_max=128, cta_max=1024, window_max=1024)
+    outs, info = _check_batch(problems, options=opt)
+    assert info["cols_cta"] + info["cols_heavy"] > 0, info
+    for (A, m) in problems[1:4]:
+        assert oracle.add(to_np(A))["terms"].max() > 48  # entries collect many terms, from several phases
