@@ -142,6 +142,7 @@ struct spkadd_handle {
   int32_t* d_search = nullptr;
   int64_t win_cap = 0;
   Counters* d_ctr = nullptr;
+  Window* d_wsort = nullptr;  // thread-block item records grouped by problem kind (batches of several kinds)
   int64_t* d_colptr = nullptr;
   long long* d_scan = nullptr;
   char* d_op = nullptr;                // one-pass: ticket counter and look-back words
@@ -306,6 +307,8 @@ static spkadd_status plan_problems(spkadd_handle** hp, bool batch, int count, co
   const size_t o_hl = cv.take<int32_t>(2 * ncols);
   const size_t o_win = cv.take<Window>(win_cap);
   const size_t o_srch = cv.take<int32_t>(win_cap);
+  const int cta_kinds = spk::num_cta_kinds(any32 && any64 ? 2 : (any64 ? 1 : 0), f32_kinds);
+  const size_t o_ws = cv.take<Window>(__builtin_popcount(cta_kinds) > 1 ? win_cap : 0);
   const size_t o_colp = cv.take<int64_t>(ncols + 1);
   const size_t o_scan = cv.take<long long>(spk::scan_tiles(ncols));
   const size_t o_op = cv.take<char>(batch ? 0 : spk::onepass_scratch_bytes(ncols));
@@ -327,6 +330,7 @@ static spkadd_status plan_problems(spkadd_handle** hp, bool batch, int count, co
   h->d_hl = reinterpret_cast<int32_t*>(h->ws + o_hl);
   h->d_win = reinterpret_cast<Window*>(h->ws + o_win);
   h->d_search = reinterpret_cast<int32_t*>(h->ws + o_srch);
+  h->d_wsort = __builtin_popcount(cta_kinds) > 1 ? reinterpret_cast<Window*>(h->ws + o_ws) : nullptr;
   h->d_colptr = reinterpret_cast<int64_t*>(h->ws + o_colp);
   h->d_scan = reinterpret_cast<long long*>(h->ws + o_scan);
   h->d_op = batch ? nullptr : h->ws + o_op;
@@ -440,6 +444,11 @@ static spkadd_status run_symbolic(spkadd_handle* h) {
       ce = spk::launch_sym_warp(h->in, h->d_wl, h->d_s, h->d_ctr, h->d_u, h->opt.warp_max, h->d_ctr, h->dev,
                                 h->st);
     h->launches += 3;
+    // Several problem kinds: the thread-block items grouped by kind for the numeric launches.
+    if (ce == cudaSuccess && h->d_wsort) {
+      ce = spk::launch_kind_sort(h->in, h->d_win, (int)h->win_cap, h->d_wsort, h->d_ctr, h->dev, h->st);
+      h->launches += 2;
+    }
   }
   if (ce == cudaSuccess) ce = spk::launch_scan(h->d_u, (int)h->ncols, h->d_scan, h->d_colptr, h->st);
   h->launches += h->ncols > 0 ? 3 : 2;
@@ -510,11 +519,13 @@ SPK_API spkadd_status spkadd_batch_symbolic(spkadd_handle* h, int64_t* nnz_B) {
 static spkadd_status run_numeric(spkadd_handle* h, const spk::Outs& out) {
   cudaError_t ce = cudaSuccess;
   const int cta_items = h->h_ctr.n_windows;
+  int item_launches = 0;
   if (cta_items > 0)
-    ce = spk::launch_num_cta(h->in, h->dt_mode, h->f32_kinds, h->d_win, cta_items, h->d_offs, h->d_colptr, out,
+    ce = spk::launch_num_cta(h->in, h->dt_mode, h->f32_kinds, h->d_win, cta_items, h->d_wsort, h->h_ctr.kind_n,
+                             h->d_offs, h->d_colptr, out,
                              h->opt.window_max > h->opt.cta_max ? h->opt.window_max : h->opt.cta_max,
-                             h->opt.block_accumulator, h->d_ctr, h->dev, h->st);
-  h->launches += (cta_items > 0) * ((h->dt_mode != 0) + (h->dt_mode != 1 ? __builtin_popcount(h->f32_kinds) : 0));
+                             h->opt.block_accumulator, h->d_ctr, h->dev, h->st, &item_launches);
+  h->launches += item_launches;
   if (ce == cudaSuccess && h->h_ctr.n_warp > 0)
     ce = spk::launch_num_warp(h->in, h->dt_mode, h->d_wl, h->d_ctr, h->h_ctr.n_warp, h->d_s, h->d_u, h->d_colptr,
                               out, h->opt.warp_max, h->opt.sort_mode, h->d_ctr, h->dev, h->st);

@@ -41,6 +41,8 @@ struct Counters {
   int32_t err;
   int32_t n_big;        // heavy columns with s_j > BIG_S (listed apart, counted in n_heavy too)
   int32_t heavy_next;   // work counter of the heavy-column symbolic kernels
+  int32_t kind_n[4];    // batches of several problem kinds: thread-block items per kind
+  int32_t kind_fill[4]; //   and their placement counters
   int32_t pad[3];
 };
 

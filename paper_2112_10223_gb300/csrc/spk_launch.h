@@ -57,10 +57,20 @@ cudaError_t launch_sym_heavy(const Inputs& in, const int32_t* list, const int32_
 cudaError_t launch_num_warp(const Inputs& in, int dt, const int32_t* list, const Counters* ctr, int n_cols,
                             const int32_t* s, const int32_t* u, const int64_t* col_ptr, const Outs& out,
                             int warp_max, int sort_mode, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
-// f32_kinds: float problems held: bit 0 k <= FP32_ACC_TERMS, bit 1 up to FP32_PHASED_MAX_K, bit 2 larger.
+// Problem kinds of the thread-block numeric launches present in a batch
+// (bit 0 float k <= FP32_ACC_TERMS, bit 1 float up to FP32_PHASED_MAX_K, bit 2
+// larger float, bit 3 double); f32_kinds holds bits 0-2 of the float problems.
+int num_cta_kinds(int dt, int f32_kinds);
+// Several kinds: copies the symbolic phase's window records (at most `cap`)
+// into wsort grouped by kind; ctr->kind_n gets the count of each.
+cudaError_t launch_kind_sort(const Inputs& in, const Window* win, int cap, Window* wsort, Counters* ctr_w,
+                             const DeviceInfo& dev, cudaStream_t st);
+// One launch per kind present: over win[0, n_win) when the batch has one
+// kind, else over the kind's group of wsort (host copy of kind_n).
 cudaError_t launch_num_cta(const Inputs& in, int dt, int f32_kinds, const Window* win, int n_win,
-                           const int32_t* offs, const int64_t* col_ptr, const Outs& out, int window_max,
-                           int accumulator, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st);
+                           const Window* wsort, const int32_t* kind_n, const int32_t* offs, const int64_t* col_ptr,
+                           const Outs& out, int window_max, int accumulator, Counters* ctr_w, const DeviceInfo& dev,
+                           cudaStream_t st, int* launches);
 // Per-problem column pointers of B (a batch): out_cp[q][j] = col_ptr[colbase + j] - col_ptr[colbase].
 cudaError_t launch_out_colptr(const Inputs& in, const Outs& o, const int64_t* col_ptr, int sms, cudaStream_t st);
 // Per-problem nnz(B): nnz[q] = col_ptr[colbase + n] - col_ptr[colbase].

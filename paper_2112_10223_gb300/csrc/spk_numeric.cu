@@ -109,6 +109,15 @@ __device__ __forceinline__ bool item_selected(int sel, const Inst* I) {
   return true;
 }
 
+// Problem kinds of the thread-block numeric launches, one launch per kind
+// present: 0 float with k <= FP32_ACC_TERMS, 1 float with
+// FP32_ACC_TERMS < k <= FP32_PHASED_MAX_K (sums in phases), 2 float with
+// larger k (double accumulators), 3 double.
+__device__ __forceinline__ int item_kind(const Inst* I) {
+  if (I->dtype == 1) return 3;
+  return I->k <= FP32_ACC_TERMS ? 0 : (I->k <= FP32_PHASED_MAX_K ? 1 : 2);
+}
+
 // Pass B of an item's slab: every entry's value added at its rank.  Without
 // phases the sums stay in acc for the caller's write (returns false).
 // PHASED (float sums of problems with k > FP32_ACC_TERMS): a slab whose
@@ -617,29 +626,109 @@ static cudaError_t launch_num_cta_t(const Inputs& in, const Window* win, int n_w
                       only_dtype, ctr_w, dev, st);
 }
 
+// Batches of several problem kinds: after the symbolic phase the
+// thread-block items' records are copied, grouped by kind (count, then place
+// with warp-aggregated appends; order inside a kind is arbitrary), so that
+// each kind's numeric launch reads only its own items.  The windows counted
+// by the symbolic kernels are read from the counters (at most `cap`).
+__global__ void k_kind_count(Inputs in, const Window* __restrict__ win, int cap, Counters* ctr_w) {
+  const int nwin = min(ctr_w->n_windows, cap);
+  int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+  for (int wi = blockIdx.x * blockDim.x + threadIdx.x; wi < nwin; wi += gridDim.x * blockDim.x) {
+    const int kd = item_kind(in.inst + inst_of(in, win[wi].col));
+    c0 += kd == 0;
+    c1 += kd == 1;
+    c2 += kd == 2;
+    c3 += kd == 3;
+  }
+  c0 = warp_sum(c0);
+  c1 = warp_sum(c1);
+  c2 = warp_sum(c2);
+  c3 = warp_sum(c3);
+  if ((threadIdx.x & 31) == 0) {
+    if (c0) atomicAdd(&ctr_w->kind_n[0], c0);
+    if (c1) atomicAdd(&ctr_w->kind_n[1], c1);
+    if (c2) atomicAdd(&ctr_w->kind_n[2], c2);
+    if (c3) atomicAdd(&ctr_w->kind_n[3], c3);
+  }
+}
+
+__global__ void k_kind_place(Inputs in, const Window* __restrict__ win, int cap, Window* __restrict__ wsort,
+                             Counters* ctr_w) {
+  __shared__ int base[4];
+  if (threadIdx.x == 0) {
+    int b = 0;
+    for (int q = 0; q < 4; ++q) {
+      base[q] = b;
+      b += ctr_w->kind_n[q];
+    }
+  }
+  __syncthreads();
+  const int nwin = min(ctr_w->n_windows, cap);
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int w0 = blockIdx.x * blockDim.x; w0 < nwin; w0 += stride) {  // (block-uniform)
+    const int wi = w0 + (int)threadIdx.x;
+    Window W{};
+    int kd = -1;
+    if (wi < nwin) {
+      W = win[wi];
+      kd = item_kind(in.inst + inst_of(in, W.col));
+    }
+    for (int q = 0; q < 4; ++q) {
+      const unsigned m = __ballot_sync(SPK_FULL, kd == q);
+      if (!m) continue;
+      const int leader = __ffs(m) - 1;
+      int pos = 0;
+      if (lane == leader) pos = atomicAdd(&ctr_w->kind_fill[q], __popc(m));
+      pos = __shfl_sync(SPK_FULL, pos, leader);
+      if (kd == q) wsort[base[q] + pos + __popc(m & ((1u << lane) - 1u))] = W;
+    }
+  }
+}
+
+int num_cta_kinds(int dt, int f32_kinds) { return (dt != 1 ? (f32_kinds & 7) : 0) | (dt != 0 ? 8 : 0); }
+
+cudaError_t launch_kind_sort(const Inputs& in, const Window* win, int cap, Window* wsort, Counters* ctr_w,
+                             const DeviceInfo& dev, cudaStream_t st) {
+  if (cap <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(&ctr_w->kind_n[0], 0, 8 * sizeof(int32_t), st);  // kind_n, kind_fill
+  if (e != cudaSuccess) return e;
+  int blocks = (cap + 255) / 256;
+  if (blocks > dev.sms * 8) blocks = dev.sms * 8;
+  k_kind_count<<<blocks, 256, 0, st>>>(in, win, cap, ctr_w);
+  k_kind_place<<<blocks, 256, 0, st>>>(in, win, cap, wsort, ctr_w);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_num_cta(const Inputs& in, int dt, int f32_kinds, const Window* win, int n_win,
-                           const int32_t* offs, const int64_t* col_ptr, const Outs& out, int window_max,
-                           int accumulator, Counters* ctr_w, const DeviceInfo& dev, cudaStream_t st) {
+                           const Window* wsort, const int32_t* kind_n, const int32_t* offs, const int64_t* col_ptr,
+                           const Outs& out, int window_max, int accumulator, Counters* ctr_w, const DeviceInfo& dev,
+                           cudaStream_t st, int* launches) {
+  *launches = 0;
   if (n_win <= 0) return cudaSuccess;
   // Float problems: k <= FP32_ACC_TERMS sum in float, up to
   // FP32_PHASED_MAX_K in float by phases, beyond in double; each kind that
-  // the batch holds gets its own launch (f32_kinds bit 0, 1, 2), which skips
-  // the other problems' items when the batch holds more than one kind.
-  const int kinds = (dt != 1 ? f32_kinds : 0) + (dt != 0 ? 8 : 0);
+  // the batch holds gets its own launch, over its own group of the records
+  // (so no launch meets another kind's items: the item filter stays off).
+  const int kinds = num_cta_kinds(dt, f32_kinds);
   const bool alone = __builtin_popcount(kinds) == 1;
+  int base = 0;
   cudaError_t e = cudaSuccess;
-  if (kinds & 1)
-    e = launch_num_cta_t<0, 0>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, alone ? -1 : 2, ctr_w,
-                               dev, st);
-  if (e == cudaSuccess && (kinds & 2))
-    e = launch_num_cta_t<0, 1>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, alone ? -1 : 3, ctr_w,
-                               dev, st);
-  if (e == cudaSuccess && (kinds & 4))
-    e = launch_num_cta_t<0, 2>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, alone ? -1 : 4, ctr_w,
-                               dev, st);
-  if (e == cudaSuccess && (kinds & 8))
-    e = launch_num_cta_t<1, 0>(in, win, n_win, offs, col_ptr, out, window_max, accumulator, alone ? -1 : 1, ctr_w,
-                               dev, st);
+  for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+    if (!((kinds >> q) & 1)) continue;
+    const Window* w = alone ? win : wsort + base;
+    const int n = alone ? n_win : kind_n[q];
+    base += alone ? 0 : kind_n[q];
+    if (n <= 0) continue;
+    ++*launches;
+    switch (q) {
+      case 0: e = launch_num_cta_t<0, 0>(in, w, n, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st); break;
+      case 1: e = launch_num_cta_t<0, 1>(in, w, n, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st); break;
+      case 2: e = launch_num_cta_t<0, 2>(in, w, n, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st); break;
+      default: e = launch_num_cta_t<1, 0>(in, w, n, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st);
+    }
+  }
   return e;
 }
 
