@@ -336,6 +336,10 @@ __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, in
   ChunkCache cc{{0, 0}, {0, 0}, false};
   for_each_column_entry<false, U, int32_t>(in, k, off, j, resident, rbeg, rlen, my_ri, nullptr, lane, fm, cc);
   __syncwarp();
+  // Every entry has set its bit: clear the whole filter for the next column
+  // (the marks are in the staged rows), so it is left zero on every path.
+#pragma unroll
+  for (int t = 0; t < FILTER_WORDS / 32; ++t) filt[t * 32 + lane] = 0u;
   constexpr int Q = 16;  // s <= 32 * Q
   // v[q] = staged row of position lane + 32q (INT32_MAX past s: no valid
   // row equals it, since rows are below m < 2^31 - 1).
@@ -350,12 +354,6 @@ __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, in
     const int32_t x = e < s ? stage[e] : INT32_MAX;
     v[q] = x & INT32_MAX;
     if (e < s) {
-      // Clear the filter for the next column: the word of the row as staged
-      // (mark bit dropped) and, for a staged value with bit 31 set, also the
-      // word of that value itself (a negative input row, which is flagged
-      // below), so the filter is left zero on every path.
-      filt[filter_hash(v[q]) >> 5] = 0u;
-      if (x < 0) filt[filter_hash(x) >> 5] = 0u;
       if (x < 0) mine |= 1u << q;
       top = max(top, (uint32_t)v[q]);
     }
