@@ -501,6 +501,15 @@ __device__ __forceinline__ int warp_column(const Inputs& in, const WarpColArgs& 
   uint32_t* cnt = sm.cnt;
   uint32_t* mlist = sm.mlist;
   const V* my_va = static_cast<const V*>(my_va_raw);
+  if (NUMERIC && resident && cur.len > 0) {
+    // The lane's value segment is first read in pass 2: start moving it into
+    // L2 now (128-byte lines), so that pass 2's loads wait on L2, not DRAM.
+    // (Prefetching the next column's segments instead ran slower: ER numeric
+    // 4.44 -> 5.1 ms.)
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(my_va + cur.beg) & ~static_cast<uintptr_t>(127);
+    const uintptr_t a1 = reinterpret_cast<uintptr_t>(my_va + cur.beg + cur.len);
+    for (uintptr_t p = a0; p < a1; p += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  }
   for (int b = lane; b < padded_words(NB); b += 32) cnt[b] = 0u;
   __syncwarp();
   // Pass 1: entries per bucket.
