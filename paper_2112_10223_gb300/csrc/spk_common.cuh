@@ -323,8 +323,10 @@ struct SegCache {
   bool valid;
 };
 
-// Inputs [k_lo, k) of the item (k_lo a multiple of 32).
-template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename FPre, typename FPost>
+// Inputs [k_lo, k) of the item (k_lo a multiple of 32).  PREF (a pass that
+// reads rows only, ahead of one that also reads values): each lane first
+// starts moving its value segment into L2.
+template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename FPre, typename FPost, bool PREF = false>
 __device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k_lo, int k, int off, SegF& seg,
                                                      FPre& fpre, FPost& fpost, SegCache& sc) {
   constexpr int NW = BLOCK / 32;
@@ -350,6 +352,14 @@ __device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k_lo,
       }
       rp = in.ri[off + i] + beg;
       if constexpr (VALS) vp = static_cast<const V*>(in.val[off + i]) + beg;
+      if constexpr (PREF) {
+        if (lw == 0 && len > 0) {  // one warp of the group per chunk
+          const uintptr_t a0 = reinterpret_cast<uintptr_t>(static_cast<const V*>(in.val[off + i]) + beg) &
+                               ~static_cast<uintptr_t>(127);
+          const uintptr_t a1 = reinterpret_cast<uintptr_t>(static_cast<const V*>(in.val[off + i]) + beg + len);
+          for (uintptr_t p = a0; p < a1; p += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+        }
+      }
     }
     if (nch <= groups) {  // this warp's only chunk: remember its bounds for the next pass
       sc.beg = beg;
@@ -421,10 +431,10 @@ __device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k_lo,
   }
 }
 
-template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename FPre, typename FPost>
+template <bool VALS, typename V, int BLOCK, int U, typename SegF, typename FPre, typename FPost, bool PREF = false>
 __device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k, int off, SegF& seg, FPre& fpre,
                                                      FPost& fpost, SegCache& sc) {
-  block_for_each_entry<VALS, V, BLOCK, U>(in, 0, k, off, seg, fpre, fpost, sc);
+  block_for_each_entry<VALS, V, BLOCK, U, SegF, FPre, FPost, PREF>(in, 0, k, off, seg, fpre, fpost, sc);
 }
 
 }  // namespace spk

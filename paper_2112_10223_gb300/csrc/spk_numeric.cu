@@ -199,7 +199,8 @@ __device__ __forceinline__ void bitmap_item(const Inputs& in, const Window& W, c
       }
     };
     SegCache sc{0, 0, false};
-    block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, setbit, mark_word, sc);
+    block_for_each_entry<false, V, BLOCK, U, decltype(seg), decltype(setbit), decltype(mark_word), true>(
+        in, k, off, seg, setbit, mark_word, sc);
     __syncthreads();
     int s_ent = 0;
     if constexpr (PHASED) block_excl_scan<BLOCK>(n_ent, reinterpret_cast<int*>(sm.red), &s_ent);
@@ -359,7 +360,8 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
       return 0u;
     };
     SegCache sc{0, 0, false};
-    block_for_each_entry<false, V, BLOCK, U>(in, k, off, seg, mark, none, sc);
+    block_for_each_entry<false, V, BLOCK, U, decltype(seg), decltype(mark), decltype(none), true>(in, k, off, seg,
+                                                                                                  mark, none, sc);
     __syncthreads();
     int s_ent = 0;
     if constexpr (PHASED) block_excl_scan<BLOCK>(n_ent, sm.red, &s_ent);
