@@ -729,6 +729,12 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_onepass(Inputs in, Onepa
         bad = true;
       } else {
         const uint32_t mul = s_mul[qb];
+        if (RES && len > 0) {  // the value segment, first read in pass 2, toward L2 now
+          const uintptr_t a0 = reinterpret_cast<uintptr_t>(static_cast<const VB*>(my_va) + beg) &
+                               ~static_cast<uintptr_t>(127);
+          const uintptr_t a1 = reinterpret_cast<uintptr_t>(static_cast<const VB*>(my_va) + beg + len);
+          for (uintptr_t p = a0; p < a1; p += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+        }
         for (int b = lane; b < padded_words(NB); b += 32) cnt[b] = 0u;
         __syncwarp();
         // Pass 1: entries per bucket; rows outside [0, m) are flagged.
