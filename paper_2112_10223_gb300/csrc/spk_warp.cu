@@ -449,7 +449,23 @@ template <typename V>
 __device__ __forceinline__ void write_sorted(const int32_t* skey, const V* sval, int s, int u, bool force_dedup,
                                              int32_t* out_row, V* out_val, Counters* ctr_w, int lane) {
   if (!force_dedup && u == s) {
-    for (int q = lane; q < s; q += 32) {
+    // Four slots per lane and round: their loads are issued before any store.
+    int q = lane;
+    for (; q + 96 < s; q += 128) {
+      int32_t r[4];
+      V v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        r[t] = skey[q + 32 * t];
+        v[t] = sval[q + 32 * t];
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        out_row[q + 32 * t] = r[t];
+        out_val[q + 32 * t] = v[t];
+      }
+    }
+    for (; q < s; q += 32) {
       out_row[q] = skey[q];
       out_val[q] = sval[q];
     }
