@@ -486,7 +486,7 @@ static spkadd_status run_symbolic(spkadd_handle* h) {
     h->d_offs = reinterpret_cast<int32_t*>(h->offs_buf);
     ce = spk::launch_window_search(h->in, h->d_win, h->d_search, (int)ns, h->d_offs, h->dev.sms, h->st);
     if (ce != cudaSuccess) return from_cuda(ce);
-    h->launches += 1;
+    h->launches += 2;
   }
   h->state = ST_SYMBOLIC;
   return SPKADD_OK;

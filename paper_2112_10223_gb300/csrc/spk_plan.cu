@@ -201,6 +201,20 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_apply(const int32_t* __rest
 // (window, input) pair (measured faster than a warp-wide 32-way search per
 // pair: with thousands of pairs in flight the per-pair setup dominates);
 // rows of the offset table are kmax inputs wide.
+// Split windows of one column partition its rows, and consecutive search rows
+// hold consecutive windows (a slab's windows are listed together, in row
+// order), so a window's end in input i is the next window's start there.
+// The search kernel finds each window's start (lower bound of r_lo) and, only
+// for a window not followed by the next window of its column, its end; the
+// second kernel copies the other ends from the next row.
+__device__ __forceinline__ bool next_window_follows(const Window* __restrict__ win,
+                                                    const int32_t* __restrict__ search_list, int n_search, int s,
+                                                    const Window& w) {
+  if (s + 1 >= n_search) return false;
+  const Window& v = win[search_list[s + 1]];
+  return v.col == w.col && v.r_lo == w.r_hi;
+}
+
 __global__ void __launch_bounds__(256) k_window_search(Inputs in, const Window* __restrict__ win,
                                                        const int32_t* __restrict__ search_list, int n_search,
                                                        int32_t* __restrict__ offs) {
@@ -216,9 +230,21 @@ __global__ void __launch_bounds__(256) k_window_search(Inputs in, const Window* 
     const int b = __ldg(cp + j), e = __ldg(cp + j + 1);
     const int32_t* ri = in.ri[I->ptr_off + i];
     const int lo = lower_bound_i32(ri, b, e, w.r_lo);
-    const int hi = lower_bound_i32(ri, lo, e, w.r_hi);
     offs[2 * t] = lo;
-    offs[2 * t + 1] = hi;
+    if (!next_window_follows(win, search_list, n_search, s, w)) offs[2 * t + 1] = lower_bound_i32(ri, lo, e, w.r_hi);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_window_ends(Inputs in, const Window* __restrict__ win,
+                                                     const int32_t* __restrict__ search_list, int n_search,
+                                                     int32_t* __restrict__ offs) {
+  const int64_t total = (int64_t)n_search * in.kmax;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int s = (int)(t / in.kmax), i = (int)(t - (int64_t)s * in.kmax);
+    const Window w = win[search_list[s]];
+    if (i >= in.inst[inst_of(in, w.col)].k) continue;
+    if (next_window_follows(win, search_list, n_search, s, w)) offs[2 * t + 1] = offs[2 * (t + in.kmax)];
   }
 }
 
@@ -303,6 +329,7 @@ cudaError_t launch_window_search(const Inputs& in, const Window* win, const int3
   int64_t blocks = (total + 255) / 256;
   if (blocks > (int64_t)sms * 32) blocks = (int64_t)sms * 32;
   k_window_search<<<(int)blocks, 256, 0, st>>>(in, win, search_list, n_search, offs);
+  k_window_ends<<<(int)blocks, 256, 0, st>>>(in, win, search_list, n_search, offs);
   return cudaGetLastError();
 }
 
