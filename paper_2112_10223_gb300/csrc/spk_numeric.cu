@@ -97,9 +97,11 @@ __device__ __forceinline__ uint32_t own_word_mask(const uint32_t* summ, int w0, 
   return per == 32 ? all : (all & ((1u << per) - 1u));
 }
 
-// Item filter of a launch that covers only some problems of a batch:
-// 0 float, 1 double, 2 float with k <= FP32_ACC_TERMS, 3 float with
-// FP32_ACC_TERMS < k <= FP32_PHASED_MAX_K, 4 float with larger k.
+// Item filter of a launch over one problem kind (a check: the records it is
+// given are grouped by kind, so it keeps them all): 0 float, 1 double, 2
+// float with k <= FP32_ACC_TERMS, 3 float with FP32_ACC_TERMS < k <=
+// FP32_PHASED_MAX_K, 4 float with larger k; -1 (a batch of one kind) keeps
+// every item.
 __device__ __forceinline__ bool item_selected(int sel, const Inst* I) {
   if (sel == 1) return I->dtype == 1;
   if (I->dtype != 0) return false;
@@ -498,8 +500,10 @@ __global__ void __launch_bounds__(BLOCK) k_num_compact(Inputs in, const Window* 
   }
 }
 
-// DT: 0 = float values, 1 = double values.  A batch mixing both runs the
-// kernel once per dtype; only_dtype >= 0 then skips the other dtype's items.
+// DT: 0 = float values, 1 = double values; ACC: 0 sums in the value type, 1
+// float sums in phases, 2 float values summed in double.  A batch of several
+// problem kinds runs the kernel once per kind over that kind's records
+// (only_dtype: the item filter above).
 template <int DT, int ACC, int BLOCK, int U>
 __global__ void __launch_bounds__(BLOCK) k_num_bitmap(Inputs in, const Window* __restrict__ win, int nwin,
                                                       const int32_t* __restrict__ offs,
@@ -712,9 +716,10 @@ cudaError_t launch_num_cta(const Inputs& in, int dt, int f32_kinds, const Window
   // Float problems: k <= FP32_ACC_TERMS sum in float, up to
   // FP32_PHASED_MAX_K in float by phases, beyond in double; each kind that
   // the batch holds gets its own launch, over its own group of the records
-  // (so no launch meets another kind's items: the item filter stays off).
+  // (the item filter of kind q, sel[q], only checks that).
   const int kinds = num_cta_kinds(dt, f32_kinds);
   const bool alone = __builtin_popcount(kinds) == 1;
+  constexpr int sel[4] = {2, 3, 4, 1};
   int base = 0;
   cudaError_t e = cudaSuccess;
   for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
@@ -724,11 +729,12 @@ cudaError_t launch_num_cta(const Inputs& in, int dt, int f32_kinds, const Window
     base += alone ? 0 : kind_n[q];
     if (n <= 0) continue;
     ++*launches;
+    const int f = alone ? -1 : sel[q];
     switch (q) {
-      case 0: e = launch_num_cta_t<0, 0>(in, w, n, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st); break;
-      case 1: e = launch_num_cta_t<0, 1>(in, w, n, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st); break;
-      case 2: e = launch_num_cta_t<0, 2>(in, w, n, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st); break;
-      default: e = launch_num_cta_t<1, 0>(in, w, n, offs, col_ptr, out, window_max, accumulator, -1, ctr_w, dev, st);
+      case 0: e = launch_num_cta_t<0, 0>(in, w, n, offs, col_ptr, out, window_max, accumulator, f, ctr_w, dev, st); break;
+      case 1: e = launch_num_cta_t<0, 1>(in, w, n, offs, col_ptr, out, window_max, accumulator, f, ctr_w, dev, st); break;
+      case 2: e = launch_num_cta_t<0, 2>(in, w, n, offs, col_ptr, out, window_max, accumulator, f, ctr_w, dev, st); break;
+      default: e = launch_num_cta_t<1, 0>(in, w, n, offs, col_ptr, out, window_max, accumulator, f, ctr_w, dev, st);
     }
   }
   return e;
