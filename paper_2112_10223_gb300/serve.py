@@ -32,7 +32,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import default_options, spkadd_batch_numeric_raw, spkadd_batch_plan_raw, spkadd_batch_symbolic, spkadd_destroy
+from . import (default_options, spkadd_batch_numeric_raw, spkadd_batch_plan_raw, spkadd_batch_symbolic,
+               spkadd_destroy, spkadd_get_info)
 
 __all__ = ["Request", "Server", "ServeStats", "output_digest"]
 
@@ -73,8 +74,15 @@ class Request:
         return self.nnz_in * (4 + sv) + (self.n + 1) * 8 + self.workspace_bytes()
 
     def workspace_bytes(self) -> int:
-        """The planner's workspace for the request (per-column and per-input tables)."""
-        return 64 * self.n + 64 * self.k + 4096
+        """An estimate of the planner's workspace for the request: per-column and per-input tables, and the
+        thread-block item records, bounded as the library bounds them for the default class limits (512 /
+        4096 / 4096), at 52 bytes each (record, search row and the copy grouped by problem kind).  After the
+        symbolic phase the server charges the batch's actual workspace instead."""
+        slabs = max(1, -(-self.m // (1 << 20)))
+        heavy = min(self.n, self.nnz_in // 4097)
+        cta = min(self.n, self.nnz_in // 513)
+        items = self.nnz_in // 4032 + heavy * (slabs + 1) + cta + 16
+        return 48 * self.n + 64 * self.k + 52 * items + 4096
 
     def output_bytes(self, nnz_out: int) -> int:
         """B's exact size once the symbolic phase has given nnz(B)."""
@@ -148,8 +156,11 @@ class Server:
                                   np.concatenate([d["ri"] for d in desc]), np.concatenate([d["va"] for d in desc]),
                                   [r.dtype for r in reqs], stream=stream, options=self.options, device=self.device)
         nnz = np.asarray(spkadd_batch_symbolic(h), dtype=np.int64)
-        # The outputs' exact size replaces their bound in the charge before they are allocated.
-        slack = sum(r.bytes_bound() - r.workspace_bytes() - r.output_bytes(int(z)) for r, z in zip(reqs, nnz))
+        # The outputs' exact size and the batch's actual workspace (with the per-input offsets of split
+        # windows, sized by the symbolic phase) replace their bounds in the charge before the outputs are
+        # allocated.
+        ws = int(spkadd_get_info(h)["workspace_bytes"])
+        slack = sum(r.bytes_bound() - r.output_bytes(int(z)) for r, z in zip(reqs, nnz)) - ws
         self._used -= slack
         charged -= slack
         n1 = np.asarray([r.n + 1 for r in reqs], dtype=np.int64)
