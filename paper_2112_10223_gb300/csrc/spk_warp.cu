@@ -372,12 +372,15 @@ __device__ __forceinline__ int warp_repeats_filtered(const Inputs& in, int k, in
   for (int i = 0; i < nmark; ++i) {
     const int em = (int)marks[i];
     const int32_t xm = stage[em] & INT32_MAX;
-    // Cheap screen first: does any of this lane's rows equal xm?
-    bool hit = false;
+    // Cheap screen first: how many of this lane's rows equal xm, the marked
+    // entry itself (in its own lane) not counted?  Most marks are hash
+    // collisions, and then no lane goes on to the exact test.
+    int eq = 0;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) hit |= v[q] == xm;
+    for (int q = 0; q < Q; ++q) eq += v[q] == xm;
+    if (lane == (em & 31)) --eq;
     bool found = false;
-    if (hit) {  // rare: the marked entry itself, and true repeats
+    if (eq > 0) {  // rare: a true repeat of the marked row
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const int e = lane + 32 * q;
