@@ -312,6 +312,14 @@ __device__ __forceinline__ const V* shfl_vptr(const V* p, int src) {
   return reinterpret_cast<const V*>(__shfl_sync(SPK_FULL, reinterpret_cast<unsigned long long>(p), src));
 }
 
+// Starts moving [p, p + bytes) toward L2 (128-byte lines) without waiting:
+// used for a value segment one pass ahead of the pass that reads it.
+__device__ __forceinline__ void l2_prefetch(const void* p, size_t bytes) {
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(p) & ~static_cast<uintptr_t>(127);
+  const uintptr_t a1 = reinterpret_cast<uintptr_t>(p) + bytes;
+  for (uintptr_t a = a0; a < a1; a += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // Ragged chunks whose segments average at least this many entries are walked
 // segment by segment instead of in flattened order.
 constexpr int SEG_MAJOR_MIN = 24;
@@ -352,14 +360,9 @@ __device__ __forceinline__ void block_for_each_entry(const Inputs& in, int k_lo,
       }
       rp = in.ri[off + i] + beg;
       if constexpr (VALS) vp = static_cast<const V*>(in.val[off + i]) + beg;
-      if constexpr (PREF) {
-        if (lw == 0 && len > 0) {  // one warp of the group per chunk
-          const uintptr_t a0 = reinterpret_cast<uintptr_t>(static_cast<const V*>(in.val[off + i]) + beg) &
-                               ~static_cast<uintptr_t>(127);
-          const uintptr_t a1 = reinterpret_cast<uintptr_t>(static_cast<const V*>(in.val[off + i]) + beg + len);
-          for (uintptr_t p = a0; p < a1; p += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-        }
-      }
+      if constexpr (PREF)
+        if (lw == 0 && len > 0)  // one warp of the group per chunk
+          l2_prefetch(static_cast<const V*>(in.val[off + i]) + beg, (size_t)len * sizeof(V));
     }
     if (nch <= groups) {  // this warp's only chunk: remember its bounds for the next pass
       sc.beg = beg;

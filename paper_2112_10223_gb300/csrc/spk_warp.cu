@@ -522,12 +522,10 @@ __device__ __forceinline__ int warp_column(const Inputs& in, const WarpColArgs& 
   const V* my_va = static_cast<const V*>(my_va_raw);
   if (NUMERIC && resident && cur.len > 0) {
     // The lane's value segment is first read in pass 2: start moving it into
-    // L2 now (128-byte lines), so that pass 2's loads wait on L2, not DRAM.
+    // L2 now, so that pass 2's loads wait on L2, not DRAM.
     // (Prefetching the next column's segments instead ran slower: ER numeric
     // 4.44 -> 5.1 ms.)
-    const uintptr_t a0 = reinterpret_cast<uintptr_t>(my_va + cur.beg) & ~static_cast<uintptr_t>(127);
-    const uintptr_t a1 = reinterpret_cast<uintptr_t>(my_va + cur.beg + cur.len);
-    for (uintptr_t p = a0; p < a1; p += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    l2_prefetch(my_va + cur.beg, (size_t)cur.len * sizeof(V));
   }
   for (int b = lane; b < padded_words(NB); b += 32) cnt[b] = 0u;
   __syncwarp();
@@ -748,12 +746,8 @@ __global__ void __launch_bounds__(WARPS * 32, 3) k_warp_onepass(Inputs in, Onepa
         bad = true;
       } else {
         const uint32_t mul = s_mul[qb];
-        if (RES && len > 0) {  // the value segment, first read in pass 2, toward L2 now
-          const uintptr_t a0 = reinterpret_cast<uintptr_t>(static_cast<const VB*>(my_va) + beg) &
-                               ~static_cast<uintptr_t>(127);
-          const uintptr_t a1 = reinterpret_cast<uintptr_t>(static_cast<const VB*>(my_va) + beg + len);
-          for (uintptr_t p = a0; p < a1; p += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-        }
+        if (RES && len > 0)  // the value segment, first read in pass 2, toward L2 now
+          l2_prefetch(static_cast<const VB*>(my_va) + beg, (size_t)len * sizeof(VB));
         for (int b = lane; b < padded_words(NB); b += 32) cnt[b] = 0u;
         __syncwarp();
         // Pass 1: entries per bucket; rows outside [0, m) are flagged.
