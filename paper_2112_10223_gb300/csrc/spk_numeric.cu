@@ -437,21 +437,23 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
       const bool written = add_values<V, A, PHASED, BLOCK, U>(in, k, off, seg, add, sc, acc, out_val + u_done, slab_u,
                                                               min(slab_u, W.u - u_done), s_ent);
       __syncthreads();
-      // Rows straight from the words (consecutive words go to consecutive
-      // ranks), values copied out coalesced.
+      // Values copied out first; then the rows, expanded from the words into
+      // the accumulator's slots (free once the values are out; a word's rows
+      // go to consecutive ranks), so that both are written coalesced.
       const int lim = min(slab_u, W.u - u_done);
       int32_t* orow = out_row + u_done;
       V* oval = out_val + u_done;
+      if (!written)
+        for (int q = threadIdx.x; q < lim; q += BLOCK) oval[q] = (V)acc[q];
+      __syncthreads();
+      int32_t* rows = reinterpret_cast<int32_t*>(acc);  // slab_u <= umax slots of at least 4 bytes
       for (int cc = threadIdx.x; cc < ne; cc += BLOCK) {
         int q = sm.wpre[cc];
         const int rbase = lo + ((int)sm.nel[cc] << 5);
-        for (uint32_t bits = sm.cw[cc]; bits; bits &= bits - 1) {
-          if (q < lim) orow[q] = rbase + __ffs(bits) - 1;
-          ++q;
-        }
+        for (uint32_t bits = sm.cw[cc]; bits; bits &= bits - 1) rows[q++] = rbase + __ffs(bits) - 1;
       }
-      if (!written)
-        for (int q = threadIdx.x; q < lim; q += BLOCK) oval[q] = (V)acc[q];
+      __syncthreads();
+      for (int q = threadIdx.x; q < lim; q += BLOCK) orow[q] = rows[q];
       u_done += slab_u;
       __syncthreads();
     }
@@ -465,7 +467,7 @@ __device__ __forceinline__ void compact_item(const Inputs& in, const Window& W, 
 }
 
 template <int DT, int ACC, int BLOCK, int U>
-__global__ void __launch_bounds__(BLOCK) k_num_compact(Inputs in, const Window* __restrict__ win, int nwin,
+__global__ void __launch_bounds__(BLOCK, (DT == 0 && ACC == 0) ? 0 : 3) k_num_compact(Inputs in, const Window* __restrict__ win, int nwin,
                                                        const int32_t* __restrict__ offs,
                                                        const int64_t* __restrict__ col_ptr, Outs o, int slab_log2,
                                                        int umax, int only_dtype, Counters* ctr_w) {
