@@ -8,6 +8,14 @@
  * of the input patterns, Sec. II-A / Alg. 5); entries whose terms cancel are
  * kept with value 0.  nnz(B) <= sum_i nnz(A_i) (Sec. II-A).
  *
+ * Values: an entry's terms are summed in an unspecified order.  Double
+ * values are summed in double.  Float values are summed so that every entry
+ * is within 1e-5 * sum|terms| of the exact sum for any k: in float while no
+ * entry can collect more than 167 terms (the float error bound
+ * (t - 1) 2^-24 sum|terms| then holds), in float phases of 128 inputs whose
+ * partial sums are added in float for k up to 4992, in double beyond;
+ * runs of repeated rows in the one-warp columns are summed in double.
+ *
  * The computation runs in phases, as the paper's k-way algorithms do:
  *   spkadd_plan      -- per-column input counts and load-balancing classes
  *                       (Sec. III-A: "in the symbolic phase we use total input
