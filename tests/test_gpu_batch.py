@@ -206,13 +206,14 @@ def test_autotuned_options_give_the_same_batch(tmp_path):
 
 
 def test_float_sums_in_phases_and_in_double_in_one_batch():
-    """One batch holding fp32 problems with k <= 167 (float sums), 167 < k <= 6912 (float sums in phases of
-    96 inputs, including a ragged last phase) and k > 6912 (double sums), plus an fp64 problem: four launches
-    of the thread-block kernels, each problem within the fp32 bound of 1e-5 * sum|terms| per entry."""
+    """One batch holding fp32 problems with k <= 167 (float sums), 167 < k <= 4992 (float sums in phases of
+    128 inputs, including a ragged last phase) and k > 4992 (double sums), plus an fp64 problem: four launches
+    of the thread-block kernels, one per kind, each problem within the fp32 bound of 1e-5 * sum|terms| per
+    entry."""
     problems = [
         (synth.spgemm_like(40, 512, 24, 16, seed=90, dtype=F32), 512),     # float, one phase
-        (synth.spgemm_like(168, 512, 24, 16, seed=91, dtype=F32), 512),    # two phases: 96 + 72
-        (synth.spgemm_like(300, 256, 20, 8, seed=92, dtype=F32), 256),     # four phases, last one 12 inputs
+        (synth.spgemm_like(168, 512, 24, 16, seed=91, dtype=F32), 512),    # two phases: 128 + 40
+        (synth.spgemm_like(300, 256, 20, 8, seed=92, dtype=F32), 256),     # three phases, the last 44 inputs
         (synth.spgemm_like(6920, 64, 3, 1, seed=93, dtype=F32), 64),       # double accumulators
         (synth.spgemm_like(200, 512, 24, 16, seed=94, dtype=F64), 512),
     ]
