@@ -657,8 +657,9 @@ def test_accumulators_heavy_column_many_subranges(acc, order):
 
 # ---------------------------------------------------------------------------
 # fp32 with many terms per output entry: past 167 inputs the thread-block
-# accumulators sum in double, and warp columns always sum a row's run in
-# double, so the 1e-5 * sum|terms| bar holds for any k.
+# accumulators sum in float phases of 128 inputs (double past k = 4992), and
+# warp columns always sum a row's run in double, so the 1e-5 * sum|terms| bar
+# holds for any k.
 # ---------------------------------------------------------------------------
 def test_fp32_k300_every_class_within_bound():
     """k = 300 SpGEMM-like fp32 inputs (each row in about a quarter of the inputs): warp, CTA and heavy items."""
